@@ -1,0 +1,152 @@
+/*
+ * CPU oracle for the swept time-space decomposition of Magee & Niemeyer,
+ * "Accelerating solutions of one-dimensional unsteady PDEs with GPU-based
+ * swept time-space decomposition" (arXiv:1705.03162).
+ *
+ * TEST INFRASTRUCTURE.  This is a plain, slow, single-threaded restatement of
+ * the paper's schemes, used only by the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg to check and time the CUDA library.  The
+ * product path never calls it and shares no code with it.
+ *
+ * Contents (all in the precision the caller selects, FP64 or FP32):
+ *  - classic decomposition (Section 5.1): one sub-timestep at a time over the
+ *    whole grid, double-buffered;
+ *  - swept decomposition restated on the CPU (Sections 4.2-4.3): nodes,
+ *    upright triangles, diamonds, edge arrays passed between nodes, closing
+ *    triangle;
+ *  - schemes: heat FTCS (Appendix A), Kuramoto-Sivashinsky with central
+ *    differences and midpoint RK2 (Appendix B), Euler equations with the
+ *    limited second-order finite-volume scheme and RK2 (Appendix C);
+ *  - boundary conditions: periodic, reflective (insulated, Appendix A) and
+ *    Dirichlet ghost cells (Appendix C).
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off (no contraction of a*b+c into FMA:
+ * every FMA is written out), no fast-math, -lm.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL 1
+#define ORC_ENOMEM 2
+#define ORC_EUNSUPPORTED 5
+
+#define ORC_HEAT 0
+#define ORC_KS 1
+#define ORC_EULER 2
+
+#define ORC_BC_PERIODIC 0
+#define ORC_BC_REFLECTIVE 1
+#define ORC_BC_DIRICHLET 2
+
+#define ORC_F64 0
+#define ORC_F32 1
+
+/* Problem description (mirrors the fields a user gives when creating a
+ * problem: equation, boundary condition, grid size, dx, dt, parameters). */
+typedef struct {
+    int32_t eq;
+    int32_t bc;
+    int64_t n_points;
+    double dx;
+    double dt;
+    double alpha;      /* heat: thermal diffusivity */
+    double gamma;      /* Euler: heat capacity ratio */
+    double left[3];    /* Euler Dirichlet end states, primitive (rho, u, p) */
+    double right[3];
+} orc_problem;
+
+/* FP64 instantiation */
+#define REAL double
+#define SFX(x) x##_f64
+#define FMA fma
+#define SQRT sqrt
+#define FABS fabs
+#include "scheme.inc"
+#undef REAL
+#undef SFX
+#undef FMA
+#undef SQRT
+#undef FABS
+
+/* FP32 instantiation */
+#define REAL float
+#define SFX(x) x##_f32
+#define FMA fmaf
+#define SQRT sqrtf
+#define FABS fabsf
+#include "scheme.inc"
+#undef REAL
+#undef SFX
+#undef FMA
+#undef SQRT
+#undef FABS
+
+static int check_problem(const orc_problem* pb)
+{
+    if (!pb || pb->n_points <= 0) return ORC_EINVAL;
+    if (pb->eq < ORC_HEAT || pb->eq > ORC_EULER) return ORC_EINVAL;
+    if (pb->bc < ORC_BC_PERIODIC || pb->bc > ORC_BC_DIRICHLET) return ORC_EINVAL;
+    if (!(pb->dx > 0) || !(pb->dt > 0)) return ORC_EINVAL;
+    int rad = pb->eq == ORC_HEAT ? 1 : 2;
+    if (pb->n_points < 2 * rad + 1) return ORC_EINVAL;
+    /* the paper's pairings: heat periodic/reflective, KS periodic, Euler
+     * Dirichlet (periodic also allowed for Euler) */
+    if (pb->eq == ORC_HEAT && pb->bc == ORC_BC_DIRICHLET) return ORC_EUNSUPPORTED;
+    if (pb->eq == ORC_KS && pb->bc != ORC_BC_PERIODIC) return ORC_EUNSUPPORTED;
+    if (pb->eq == ORC_EULER && pb->bc == ORC_BC_REFLECTIVE) return ORC_EUNSUPPORTED;
+    return ORC_OK;
+}
+
+/* Advance `state` (nv x N, SoA, in place) by `steps` timesteps with the
+ * classic decomposition. */
+int orc_classic(const orc_problem* pb, int32_t dtype, void* state, int64_t steps)
+{
+    int e = check_problem(pb);
+    if (e) return e;
+    if (!state || steps < 0) return ORC_EINVAL;
+    if (dtype == ORC_F64) return classic_f64(pb, (double*)state, steps);
+    if (dtype == ORC_F32) return classic_f32(pb, (float*)state, steps);
+    return ORC_EINVAL;
+}
+
+/* Advance `state` by `steps` timesteps with the swept decomposition, nodes of
+ * n points (N % n == 0, n / (2 rad) even). */
+int orc_swept(const orc_problem* pb, int32_t dtype, void* state, int64_t steps, int64_t n)
+{
+    int e = check_problem(pb);
+    if (e) return e;
+    if (!state || steps < 0) return ORC_EINVAL;
+    if (dtype == ORC_F64) return swept_f64(pb, (double*)state, steps, n);
+    if (dtype == ORC_F32) return swept_f32(pb, (float*)state, steps, n);
+    return ORC_EINVAL;
+}
+
+/* Pieces of the Euler scheme, exposed for the pins that check them on
+ * hand-worked states (FP64).  q: conserved (rho, rho u, E) triples. */
+double orc_euler_pressure_f64(const double* q, double gamma)
+{
+    return euler_pressure_f64(q[0], q[1], q[2], gamma - 1.0, NULL);
+}
+
+/* q: 4 cells (a-1, a, b, b+1) x 3; outputs the reconstructed left and right
+ * states at the interface between a and b. */
+int orc_euler_reconstruct_f64(const double* q, double gamma, double* ql, double* qr)
+{
+    double gm1 = gamma - 1.0, p[4];
+    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL);
+    euler_reconstruct_f64(q + 3, q + 6, p[0], p[1], p[2], p[3], ql, qr);
+    return ORC_OK;
+}
+
+/* G = 2 Flux at the interface between cells a and b of the 4 cells q. */
+int orc_euler_interface_f64(const double* q, double gamma, double* G)
+{
+    double gm1 = gamma - 1.0, ggm1 = gamma * (gamma - 1.0);
+    double p[4];
+    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL);
+    euler_interface_f64(q + 3, q + 6, p[0], p[1], p[2], p[3], gm1, ggm1, G);
+    return ORC_OK;
+}
