@@ -1,0 +1,173 @@
+/*
+ * swept.h -- C ABI of the GB300 (sm_103a) swept time-space decomposition
+ * library, libswept.so.
+ *
+ * The library solves the paper's three explicit 1D test problems
+ * (Magee & Niemeyer, arXiv:1705.03162, Section 5.2 and Appendices A-C):
+ *   heat  u_t = alpha u_xx, FTCS                          (Appendix A)
+ *   KS    u_t + u u_x + u_xx + u_xxxx = 0, central
+ *         differences, midpoint RK2                       (Appendix B)
+ *   Euler Sod shock tube, limited second-order finite
+ *         volume, Rusanov flux, midpoint RK2              (Appendix C)
+ * with either the classic decomposition (one kernel per sub-timestep,
+ * Section 5.1) or the swept decomposition (upright triangle, diamonds, closing
+ * triangle; Sections 4.2-4.3).  Both schemes evaluate every point update with
+ * the same device function, so for the same problem they produce the same
+ * bits.
+ *
+ * Conventions
+ *  - Layout: the state is structure-of-arrays [nv][N] of double (SWP_F64) or
+ *    float (SWP_F32), nv = 3 for Euler (rho, rho u, E), else 1.
+ *  - Ownership: the library owns all device memory of a problem (allocated in
+ *    swp_create, freed in swp_destroy).  Caller buffers are only read or
+ *    written during the call that receives them (host buffers) or during the
+ *    stream work that call enqueues (device buffers).
+ *  - Streams: every call enqueues its GPU work on the problem's stream (the
+ *    one given to swp_create; NULL = the legacy default stream).  Calls with a
+ *    host buffer synchronise that stream before returning.
+ *  - Errors: every call returns a swp_status; nothing throws across the ABI.
+ *    swp_last_error() returns a thread-local description of the last error.
+ *  - Threading: a problem may be used from one host thread at a time.
+ */
+#ifndef SWEPT_H
+#define SWEPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SWP_OK = 0,
+    SWP_EINVAL = 1,        /* invalid argument (null, size, node width, ...) */
+    SWP_ENOMEM = 2,        /* device or host allocation failed */
+    SWP_EBUDGET = 3,       /* request exceeds the caller-set memory budget */
+    SWP_ECUDA = 4,         /* a CUDA runtime call failed */
+    SWP_EUNSUPPORTED = 5,  /* equation / boundary / precision not supported */
+    SWP_ETIMEOUT = 6,      /* a device-side bounded wait gave up */
+    SWP_EDEVICE = 7        /* no usable sm_103 device */
+} swp_status;
+
+typedef enum { SWP_HEAT = 0, SWP_KS = 1, SWP_EULER = 2 } swp_equation;
+
+/* Boundary conditions: periodic; reflective (insulated ends, mirror about the
+ * end points: u_{-k} = u_k, u_{N-1+k} = u_{N-1-k}, Appendix A Eq. heatcond);
+ * Dirichlet (two ghost cells per side holding the end states, Appendix C).
+ * Supported pairs: heat periodic/reflective, KS periodic, Euler
+ * Dirichlet/periodic. */
+typedef enum { SWP_BC_PERIODIC = 0, SWP_BC_REFLECTIVE = 1, SWP_BC_DIRICHLET = 2 } swp_bc;
+
+typedef enum { SWP_F64 = 0, SWP_F32 = 1 } swp_dtype;   /* Euler: SWP_F64 only */
+
+typedef enum { SWP_CLASSIC = 0, SWP_SWEPT = 1 } swp_scheme;
+
+/* Problem description.
+ *   n_points : N grid points (cells for Euler), N >= 5
+ *   dx, dt   : grid spacing and timestep (> 0)
+ *   alpha    : heat diffusivity (Fourier number alpha dt / dx^2)
+ *   gamma    : Euler heat capacity ratio
+ *   left, right : Euler Dirichlet end states, primitive (rho, u, p) */
+typedef struct {
+    int32_t eq;        /* swp_equation */
+    int32_t bc;        /* swp_bc */
+    int32_t dtype;     /* swp_dtype */
+    int32_t reserved;  /* must be 0 */
+    int64_t n_points;
+    double dx;
+    double dt;
+    double alpha;
+    double gamma;
+    double left[3];
+    double right[3];
+} swp_desc;
+
+/* How swp_advance_ex runs the swept scheme. */
+typedef enum {
+    SWP_LAUNCH_AUTO = 0,        /* library choice */
+    SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
+                                   nodes synchronise at kernel boundaries */
+    SWP_LAUNCH_PERSISTENT = 2   /* one kernel for the whole advance; each node
+                                   waits (bounded) on its two neighbours' flags */
+} swp_launch;
+
+typedef struct {
+    int32_t scheme;            /* swp_scheme */
+    int32_t points_per_block;  /* swept node width n (0 = auto); classic: unused */
+    int32_t launch;            /* swp_launch */
+    int32_t threads;           /* threads per block (0 = auto; multiple of 32) */
+} swp_advance_opts;
+
+typedef struct swp_problem swp_problem;
+
+/* Create a problem on the current CUDA device and copy its initial state.
+ *   desc         : problem description (copied)
+ *   u0           : nv * N values of the dtype, layout [nv][N]
+ *   u0_on_device : 0 = u0 is host memory, 1 = device memory
+ *   cuda_stream  : cudaStream_t for all work of this problem (NULL = default)
+ *   out          : receives the handle
+ * Errors: SWP_EINVAL (null / bad sizes), SWP_EUNSUPPORTED (bad pairing),
+ * SWP_EBUDGET (see swp_set_memory_budget), SWP_ENOMEM, SWP_EDEVICE, SWP_ECUDA. */
+swp_status swp_create(const swp_desc* desc, const void* u0, int u0_on_device,
+                      void* cuda_stream, swp_problem** out);
+
+/* Replace the state by nv * N values from src (bytes = nv * N * sizeof(dtype)). */
+swp_status swp_write(swp_problem* p, const void* src, size_t src_bytes, int src_on_device);
+
+/* Advance n_steps timesteps (any n_steps >= 0) with `scheme`.
+ * Swept: points_per_block = n must divide N, be a multiple of 4 * radius
+ * (radius 1 for heat, 2 for KS/Euler) and leave every node's working set in
+ * shared memory; 0 picks a width.  The advance ends on a closing triangle, so
+ * the state is complete afterwards (Section 4.2: output only at closing
+ * triangles); a final partial half-cycle is closed exactly.
+ * Asynchronous on the problem's stream.  SWP_ETIMEOUT reports a persistent
+ * launch whose bounded neighbour wait gave up (the state is then invalid). */
+swp_status swp_advance(swp_problem* p, int64_t n_steps, int32_t scheme, int32_t points_per_block);
+swp_status swp_advance_ex(swp_problem* p, int64_t n_steps, const swp_advance_opts* opts);
+
+/* Copy the current state (nv * N values, [nv][N]) to dst.  dst_bytes must be
+ * at least nv * N * sizeof(dtype).  Host dst: synchronises the stream. */
+swp_status swp_read(swp_problem* p, void* dst, size_t dst_bytes, int dst_on_device);
+
+/* Wait for the problem's stream; reports a deferred device-side error. */
+swp_status swp_synchronize(swp_problem* p);
+
+/* Free all device memory of the problem.  NULL is accepted (no-op). */
+swp_status swp_destroy(swp_problem* p);
+
+/* Number of points N, variables nv and element size of a problem. */
+swp_status swp_shape(const swp_problem* p, int64_t* n_points, int32_t* nv, int32_t* elem_bytes);
+
+/* Kernels launched by this problem since creation (for launch accounting). */
+int64_t swp_kernel_launches(const swp_problem* p);
+
+/* Device memory a problem of this description would allocate, in bytes. */
+swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes);
+
+/* Process-wide device-memory budget for swp_create (0 = unlimited): a create
+ * whose allocation would push the library's live total above it fails with
+ * SWP_EBUDGET. */
+swp_status swp_set_memory_budget(size_t bytes);
+size_t swp_memory_in_use(void);
+
+/* Fault-injection hook for tests of the persistent launch's bounded waits.
+ * withhold != 0 makes every neighbour wait of later SWP_LAUNCH_PERSISTENT
+ * advances of this problem wait for a flag value no node ever publishes, so
+ * each wait gives up after wait_limit_ns nanoseconds (device global timer),
+ * the kernel returns without computing, and the next swp_synchronize /
+ * swp_read reports SWP_ETIMEOUT (the state is then invalid).  withhold = 0
+ * restores normal waits; wait_limit_ns (in (0, 1e10]) bounds every wait of
+ * later persistent advances either way (default 2 s).  Nothing faults, traps
+ * or hangs.  The paper has no counterpart: its nodes synchronise only at
+ * kernel boundaries (Section 3). */
+swp_status swp_debug_withhold_flags(swp_problem* p, int withhold, int64_t wait_limit_ns);
+
+const char* swp_status_str(swp_status s);
+const char* swp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWEPT_H */

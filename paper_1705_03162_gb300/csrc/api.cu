@@ -1,0 +1,545 @@
+// C ABI of libswept.so (declared in include/swept.h).  Host-side driver of the
+// classic (one launch per sub-timestep, arXiv:1705.03162 Section 5.1) and the
+// swept (triangle / diamond / closing phases, Sections 4.2-4.3) schemes.
+// Built with host FP contraction off so the coefficients below round exactly
+// as written.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/swept.h"
+#include "launch.h"
+
+using namespace swp;
+
+struct swp_problem {
+    swp_desc desc;
+    int nv = 1, rad = 1, sub = 1, esize = 8;
+    int64_t N = 0;
+    void* rows[2] = {nullptr, nullptr};   // level rows / classic ping-pong, [nv][N] each
+    int cur = 0;                          // which row holds the state
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sms = 0;
+    int64_t launches = 0;
+    size_t bytes = 0;
+    Coefs<double> cd{};
+    Coefs<float> cf{};
+    // persistent swept launch
+    uint32_t* flags = nullptr;
+    int flags_k = 0;          // capacity of flags
+    int flags_last_k = -1;    // node count the flags were last used with
+    uint32_t flag_base = 0;
+    int inject_withheld_flags = 0;            // test hook: waits never succeed
+    uint64_t wait_limit_ns = 2000000000ull;   // bound of one neighbour wait
+    unsigned int* counter = nullptr;
+    int* status = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<size_t> g_in_use{0};
+std::atomic<size_t> g_budget{0};
+
+swp_status fail(swp_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+swp_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(SWP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int radius_of(int eq) { return eq == SWP_HEAT ? 1 : 2; }
+int nv_of(int eq) { return eq == SWP_EULER ? 3 : 1; }
+int esize_of(int dtype) { return dtype == SWP_F32 ? 4 : 8; }
+
+swp_status check_desc(const swp_desc* d)
+{
+    if (!d) return fail(SWP_EINVAL, "desc is NULL");
+    if (d->eq < SWP_HEAT || d->eq > SWP_EULER) return fail(SWP_EINVAL, "unknown equation %d", d->eq);
+    if (d->bc < SWP_BC_PERIODIC || d->bc > SWP_BC_DIRICHLET)
+        return fail(SWP_EINVAL, "unknown boundary condition %d", d->bc);
+    if (d->dtype != SWP_F64 && d->dtype != SWP_F32) return fail(SWP_EINVAL, "unknown dtype %d", d->dtype);
+    if (d->reserved != 0) return fail(SWP_EINVAL, "reserved field must be 0");
+    if (d->n_points < 5) return fail(SWP_EINVAL, "n_points must be >= 5 (got %lld)", (long long)d->n_points);
+    if (d->n_points > (int64_t)1 << 34) return fail(SWP_EINVAL, "n_points too large");
+    if (!(d->dx > 0) || !(d->dt > 0) || !std::isfinite(d->dx) || !std::isfinite(d->dt))
+        return fail(SWP_EINVAL, "dx and dt must be finite and > 0");
+    if (d->eq == SWP_HEAT && d->bc == SWP_BC_DIRICHLET)
+        return fail(SWP_EUNSUPPORTED, "heat supports periodic and reflective ends");
+    if (d->eq == SWP_KS && d->bc != SWP_BC_PERIODIC)
+        return fail(SWP_EUNSUPPORTED, "KS supports periodic ends");
+    if (d->eq == SWP_EULER && d->bc == SWP_BC_REFLECTIVE)
+        return fail(SWP_EUNSUPPORTED, "Euler supports Dirichlet and periodic ends");
+    if (d->eq == SWP_EULER && d->dtype != SWP_F64)
+        return fail(SWP_EUNSUPPORTED, "Euler runs in FP64 only");
+    if (d->eq == SWP_HEAT && !std::isfinite(d->alpha)) return fail(SWP_EINVAL, "alpha must be finite");
+    if (d->eq == SWP_EULER && !(d->gamma > 1.0)) return fail(SWP_EINVAL, "gamma must be > 1");
+    return SWP_OK;
+}
+
+size_t state_bytes(const swp_desc* d) { return (size_t)nv_of(d->eq) * d->n_points * esize_of(d->dtype); }
+
+// Coefficients of the point updates, formed in double and rounded once.
+template <typename R>
+void make_coefs(const swp_desc* d, Coefs<R>& c)
+{
+    std::memset(&c, 0, sizeof(c));
+    const double fo = d->alpha * d->dt / (d->dx * d->dx);
+    c.fo = (R)fo;
+    for (int s = 0; s < 2; ++s) {
+        const double h = s == 0 ? 0.5 * d->dt : d->dt;
+        const double c1 = 1.0 / (4.0 * d->dx);
+        const double c2 = 1.0 / (d->dx * d->dx);
+        const double c4 = c2 * c2;
+        const double a1 = -(h * c1), a2 = -(h * c2), a4 = -(h * c4);
+        c.a1[s] = (R)a1;
+        c.a4[s] = (R)a4;
+        c.beta[s] = (R)(a2 - 4.0 * a4);
+        const double lam = d->dt / d->dx;
+        const double lamh = s == 0 ? 0.5 * lam : lam;
+        c.kh[s] = (R)(-(0.5 * lamh));
+    }
+    const double g = d->gamma;
+    c.gm1 = (R)(g - 1.0);
+    c.ggm1 = (R)(g * (g - 1.0));
+    const double* st[2] = {d->left, d->right};
+    R* gh[2] = {c.ghost_l, c.ghost_r};
+    for (int s = 0; s < 2; ++s) {
+        const double r = st[s][0], u = st[s][1], p = st[s][2];
+        gh[s][0] = (R)r;
+        gh[s][1] = (R)(r * u);
+        gh[s][2] = (R)(p / (g - 1.0) + 0.5 * r * u * u);
+    }
+}
+
+// Largest shared memory a block may use on this device.
+size_t max_smem(int device)
+{
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    return (size_t)v;
+}
+
+// A swept node width must divide N, be a multiple of 4 rad (so that H is
+// even) and fit the node's working set in shared memory.
+swp_status check_width(const swp_problem* p, int n)
+{
+    const int step = 4 * p->rad;
+    if (n < step || n % step) return fail(SWP_EINVAL, "points_per_block %d must be a positive multiple of %d", n, step);
+    if (p->N % n) return fail(SWP_EINVAL, "points_per_block %d must divide n_points %lld", n, (long long)p->N);
+    if (swept_smem_bytes(p->desc.eq, n, p->esize) > max_smem(p->device))
+        return fail(SWP_EINVAL, "points_per_block %d needs %zu bytes of shared memory (max %zu)", n,
+                    swept_smem_bytes(p->desc.eq, n, p->esize), max_smem(p->device));
+    return SWP_OK;
+}
+
+// Default node width: enough nodes to cover every SM twice when N allows,
+// at most 1024 points (512 for Euler), at least 32.
+int default_width(const swp_problem* p)
+{
+    const int step = 4 * p->rad;
+    const int cap = p->desc.eq == SWP_EULER ? 512 : 1024;
+    int64_t target = p->N / (2 * (int64_t)(p->sms > 0 ? p->sms : 152));
+    if (target > cap) target = cap;
+    if (target < 32) target = 32;
+    for (int64_t n = target; n >= step; --n)
+        if (n % step == 0 && p->N % n == 0 && check_width(p, (int)n) == SWP_OK) return (int)n;
+    for (int64_t n = target + 1; n <= cap && n <= p->N; ++n)
+        if (n % step == 0 && p->N % n == 0 && check_width(p, (int)n) == SWP_OK) return (int)n;
+    return 0;
+}
+
+template <typename R>
+const Coefs<R>& coefs_of(const swp_problem* p);
+template <>
+const Coefs<double>& coefs_of<double>(const swp_problem* p) { return p->cd; }
+template <>
+const Coefs<float>& coefs_of<float>(const swp_problem* p) { return p->cf; }
+
+template <typename R>
+swp_status run_classic(swp_problem* p, int64_t steps, int threads)
+{
+    if (threads <= 0) threads = 256;
+    if (threads > 256 || threads % 32) return fail(SWP_EINVAL, "classic threads must be a multiple of 32 <= 256");
+    const Coefs<R>& c = coefs_of<R>(p);
+    const int eq = p->desc.eq, bc = p->desc.bc;
+    for (int64_t m = 0; m < steps; ++m) {
+        R* u = (R*)p->rows[p->cur];
+        R* o = (R*)p->rows[1 - p->cur];
+        cudaError_t e;
+        if (eq == SWP_HEAT) {
+            e = launch_classic<R>(eq, bc, u, u, o, p->N, 0, c, threads, p->stream);
+            p->launches++;
+            if (e != cudaSuccess) return cuda_fail(e, "classic heat launch");
+            p->cur = 1 - p->cur;
+        } else {
+            e = launch_classic<R>(eq, bc, u, u, o, p->N, 0, c, threads, p->stream);
+            p->launches++;
+            if (e != cudaSuccess) return cuda_fail(e, "classic predictor launch");
+            e = launch_classic<R>(eq, bc, o, u, u, p->N, 1, c, threads, p->stream);
+            p->launches++;
+            if (e != cudaSuccess) return cuda_fail(e, "classic final launch");
+        }
+    }
+    return SWP_OK;
+}
+
+struct SweptPlan {
+    int n, H, K;
+    int64_t T, Q, r, n_phases;
+    int top;   // relative level of the last phase's top row
+};
+
+SweptPlan plan_swept(const swp_problem* p, int64_t steps, int n)
+{
+    SweptPlan s;
+    s.n = n;
+    s.H = n / (2 * p->rad);
+    s.K = (int)(p->N / n);
+    s.T = steps * p->sub;
+    s.Q = s.T / s.H;
+    s.r = s.T % s.H;
+    s.n_phases = s.r > 0 ? s.Q + 2 : s.Q + 1;
+    s.top = s.r > 0 ? (int)s.r : s.H;
+    return s;
+}
+
+template <typename R>
+swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads)
+{
+    R* A = (R*)p->rows[p->cur];
+    R* B = (R*)p->rows[1 - p->cur];
+    const Coefs<R>& c = coefs_of<R>(p);
+    for (int64_t ph = 0; ph < s.n_phases; ++ph) {
+        PhaseGeom g;
+        g.N = p->N;
+        g.n = s.n;
+        g.H = s.H;
+        g.K = s.K;
+        g.j_lo = ph == 0 ? s.H + 1 : 1;
+        g.j_hi = ph < s.Q ? 2 * s.H - 1 : (ph == s.Q ? s.H + (int)s.r : (int)s.r);
+        g.odd = (int)(ph & 1);
+        cudaError_t e = launch_swept_phase<R>(p->desc.eq, p->desc.bc, A, B, g, c, threads, p->stream);
+        p->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "swept phase launch");
+    }
+    return SWP_OK;
+}
+
+swp_status ensure_persistent_state(swp_problem* p, int K)
+{
+    if (p->flags && p->flags_k >= K) return SWP_OK;
+    if (p->flags) cudaFree(p->flags);
+    p->flags = nullptr;
+    cudaError_t e = cudaMalloc(&p->flags, sizeof(uint32_t) * (size_t)K);
+    if (e != cudaSuccess) return fail(SWP_ENOMEM, "flags: %s", cudaGetErrorString(e));
+    e = cudaMemsetAsync(p->flags, 0, sizeof(uint32_t) * (size_t)K, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flags memset");
+    p->flags_k = K;
+    p->flag_base = 0;
+    if (!p->counter) {
+        e = cudaMalloc(&p->counter, sizeof(unsigned int) + sizeof(int) * 4);
+        if (e != cudaSuccess) return fail(SWP_ENOMEM, "counter: %s", cudaGetErrorString(e));
+        p->status = reinterpret_cast<int*>(p->counter + 1);
+        e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned int) + sizeof(int) * 4, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "status memset");
+    }
+    return SWP_OK;
+}
+
+template <typename R>
+swp_status run_swept_persistent(swp_problem* p, const SweptPlan& s, int threads)
+{
+    swp_status st = ensure_persistent_state(p, s.K);
+    if (st != SWP_OK) return st;
+    // flags count completed phases per node; restart the count when the node
+    // layout changes or the count would wrap
+    if (p->flags_last_k != s.K || (uint64_t)p->flag_base + (uint64_t)s.n_phases >= (1ull << 30)) {
+        cudaError_t e = cudaMemsetAsync(p->flags, 0, sizeof(uint32_t) * (size_t)p->flags_k, p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "flags reset");
+        p->flag_base = 0;
+        p->flags_last_k = s.K;
+    }
+    const int64_t total = s.n_phases * (int64_t)s.K;
+    if (total >= ((int64_t)1 << 31)) return fail(SWP_EINVAL, "advance too long for one persistent launch");
+    const int bps = swept_persistent_blocks_per_sm<R>(p->desc.eq, s.n, threads);
+    if (bps <= 0) return fail(SWP_EINVAL, "persistent kernel does not fit (n=%d, threads=%d)", s.n, threads);
+    int64_t blocks = (int64_t)p->sms * bps;
+    if (blocks > total) blocks = total;
+    PersistentPlan plan;
+    plan.N = p->N;
+    plan.n = s.n;
+    plan.H = s.H;
+    plan.K = s.K;
+    plan.Q = s.Q;
+    plan.r = s.r;
+    plan.n_phases = s.n_phases;
+    plan.flag_base = p->flag_base;
+    plan.wait_offset = p->inject_withheld_flags ? (1u << 30) : 0u;
+    plan.wait_limit_ns = p->wait_limit_ns;
+    cudaError_t e = launch_swept_persistent<R>(p->desc.eq, p->desc.bc, (R*)p->rows[p->cur],
+                                               (R*)p->rows[1 - p->cur], plan, coefs_of<R>(p), p->flags,
+                                               p->counter, p->status, threads, (int)blocks, p->stream);
+    p->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "persistent swept launch");
+    p->flag_base += (uint32_t)s.n_phases;
+    return SWP_OK;
+}
+
+// Reads the device status word of persistent launches (stream must be idle).
+swp_status check_device_status(swp_problem* p)
+{
+    if (!p->status) return SWP_OK;
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (st != 0) {
+        cudaMemset(p->status, 0, sizeof(int));
+        p->flags_last_k = -1;   // flags are inconsistent: restart them next time
+        return fail(SWP_ETIMEOUT, "a node's bounded wait for its neighbours gave up; the state is invalid");
+    }
+    return SWP_OK;
+}
+
+template <typename R>
+swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& o)
+{
+    if (o.scheme == SWP_CLASSIC) return run_classic<R>(p, steps, o.threads);
+    int n = o.points_per_block;
+    if (n == 0) {
+        n = default_width(p);
+        if (n == 0) return fail(SWP_EINVAL, "no valid node width for n_points %lld", (long long)p->N);
+    }
+    swp_status st = check_width(p, n);
+    if (st != SWP_OK) return st;
+    int threads = o.threads;
+    if (threads == 0) threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
+    const int max_threads = p->desc.eq == SWP_EULER ? 256 : 1024;
+    if (threads < 32 || threads > max_threads || threads % 32)
+        return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
+    const SweptPlan s = plan_swept(p, steps, n);
+    if (s.T == 0) return SWP_OK;
+    int launch = o.launch == SWP_LAUNCH_AUTO ? SWP_LAUNCH_PER_PHASE : o.launch;
+    if (launch == SWP_LAUNCH_PERSISTENT) st = run_swept_persistent<R>(p, s, threads);
+    else if (launch == SWP_LAUNCH_PER_PHASE) st = run_swept_phases<R>(p, s, threads);
+    else return fail(SWP_EINVAL, "unknown launch mode %d", o.launch);
+    if (st != SWP_OK) return st;
+    if (s.top & 1) p->cur = 1 - p->cur;   // last level odd: the state is in row B
+    return SWP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!bytes) return fail(SWP_EINVAL, "bytes is NULL");
+    *bytes = 2 * state_bytes(desc);
+    return SWP_OK;
+}
+
+swp_status swp_set_memory_budget(size_t bytes)
+{
+    g_budget.store(bytes);
+    return SWP_OK;
+}
+
+size_t swp_memory_in_use(void) { return g_in_use.load(); }
+
+swp_status swp_create(const swp_desc* desc, const void* u0, int u0_on_device, void* cuda_stream,
+                      swp_problem** out)
+{
+    if (!out) return fail(SWP_EINVAL, "out is NULL");
+    *out = nullptr;
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!u0) return fail(SWP_EINVAL, "u0 is NULL");
+    // admission against the memory budget comes first (host-side decision)
+    const size_t sbytes = state_bytes(desc);
+    const size_t need = 2 * sbytes;
+    const size_t budget = g_budget.load();
+    size_t cur = g_in_use.load();
+    for (;;) {
+        if (budget && cur + need > budget)
+            return fail(SWP_EBUDGET, "problem needs %zu bytes, %zu of the %zu-byte budget in use", need, cur, budget);
+        if (g_in_use.compare_exchange_weak(cur, cur + need)) break;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) {
+        g_in_use -= need;
+        return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (prop.major != 10 || prop.minor != 3) {
+        g_in_use -= need;
+        return fail(SWP_EDEVICE, "libswept is built for sm_103 (device is sm_%d%d)", prop.major, prop.minor);
+    }
+    swp_problem* p = new (std::nothrow) swp_problem();
+    if (!p) {
+        g_in_use -= need;
+        return fail(SWP_ENOMEM, "host allocation failed");
+    }
+    p->desc = *desc;
+    p->nv = nv_of(desc->eq);
+    p->rad = radius_of(desc->eq);
+    p->sub = desc->eq == SWP_HEAT ? 1 : 2;
+    p->esize = esize_of(desc->dtype);
+    p->N = desc->n_points;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->device = dev;
+    p->sms = prop.multiProcessorCount;
+    p->bytes = need;
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, need);
+    if (e != cudaSuccess) {
+        g_in_use -= need;
+        delete p;
+        return fail(SWP_ENOMEM, "device allocation of %zu bytes failed: %s", need, cudaGetErrorString(e));
+    }
+    p->rows[0] = mem;
+    p->rows[1] = (char*)mem + sbytes;
+    make_coefs<double>(desc, p->cd);
+    make_coefs<float>(desc, p->cf);
+    e = cudaMemsetAsync(p->rows[1], 0, sbytes, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->rows[0], u0, sbytes,
+                            u0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && !u0_on_device) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        swp_destroy(p);
+        return cuda_fail(e, "initial state copy");
+    }
+    *out = p;
+    return SWP_OK;
+}
+
+swp_status swp_write(swp_problem* p, const void* src, size_t src_bytes, int src_on_device)
+{
+    if (!p || !src) return fail(SWP_EINVAL, "problem or src is NULL");
+    const size_t sbytes = (size_t)p->nv * p->N * p->esize;
+    if (src_bytes != sbytes) return fail(SWP_EINVAL, "src_bytes %zu != state bytes %zu", src_bytes, sbytes);
+    cudaError_t e = cudaMemcpyAsync(p->rows[p->cur], src, sbytes,
+                                    src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    p->stream);
+    if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state write");
+    return SWP_OK;
+}
+
+swp_status swp_advance_ex(swp_problem* p, int64_t n_steps, const swp_advance_opts* opts)
+{
+    if (!p || !opts) return fail(SWP_EINVAL, "problem or opts is NULL");
+    if (n_steps < 0) return fail(SWP_EINVAL, "n_steps must be >= 0");
+    if (opts->scheme != SWP_CLASSIC && opts->scheme != SWP_SWEPT)
+        return fail(SWP_EINVAL, "unknown scheme %d", opts->scheme);
+    if (n_steps == 0) return SWP_OK;
+    if (n_steps > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps too large");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device)
+        return fail(SWP_EINVAL, "current device %d differs from the problem's device %d", dev, p->device);
+    if (p->desc.dtype == SWP_F64) return advance_typed<double>(p, n_steps, *opts);
+    return advance_typed<float>(p, n_steps, *opts);
+}
+
+swp_status swp_advance(swp_problem* p, int64_t n_steps, int32_t scheme, int32_t points_per_block)
+{
+    swp_advance_opts o;
+    o.scheme = scheme;
+    o.points_per_block = points_per_block;
+    o.launch = SWP_LAUNCH_AUTO;
+    o.threads = 0;
+    return swp_advance_ex(p, n_steps, &o);
+}
+
+swp_status swp_synchronize(swp_problem* p)
+{
+    if (!p) return fail(SWP_EINVAL, "problem is NULL");
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return check_device_status(p);
+}
+
+swp_status swp_read(swp_problem* p, void* dst, size_t dst_bytes, int dst_on_device)
+{
+    if (!p || !dst) return fail(SWP_EINVAL, "problem or dst is NULL");
+    const size_t sbytes = (size_t)p->nv * p->N * p->esize;
+    if (dst_bytes < sbytes) return fail(SWP_EINVAL, "dst_bytes %zu < state bytes %zu", dst_bytes, sbytes);
+    cudaError_t e = cudaMemcpyAsync(dst, p->rows[p->cur], sbytes,
+                                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "state read");
+    if (!dst_on_device) return swp_synchronize(p);
+    return SWP_OK;
+}
+
+swp_status swp_destroy(swp_problem* p)
+{
+    if (!p) return SWP_OK;
+    cudaError_t e = cudaSuccess;
+    if (p->rows[0]) e = cudaFree(p->rows[0]);
+    if (p->flags) cudaFree(p->flags);
+    if (p->counter) cudaFree(p->counter);
+    g_in_use -= p->bytes;
+    delete p;
+    if (e != cudaSuccess) return cuda_fail(e, "free");
+    return SWP_OK;
+}
+
+swp_status swp_shape(const swp_problem* p, int64_t* n_points, int32_t* nv, int32_t* elem_bytes)
+{
+    if (!p) return fail(SWP_EINVAL, "problem is NULL");
+    if (n_points) *n_points = p->N;
+    if (nv) *nv = p->nv;
+    if (elem_bytes) *elem_bytes = p->esize;
+    return SWP_OK;
+}
+
+int64_t swp_kernel_launches(const swp_problem* p) { return p ? p->launches : -1; }
+
+swp_status swp_debug_withhold_flags(swp_problem* p, int withhold, int64_t wait_limit_ns)
+{
+    if (!p) return fail(SWP_EINVAL, "problem is NULL");
+    if (wait_limit_ns <= 0 || wait_limit_ns > 10000000000ll)
+        return fail(SWP_EINVAL, "wait_limit_ns must be in (0, 1e10]");
+    p->inject_withheld_flags = withhold ? 1 : 0;
+    p->wait_limit_ns = (uint64_t)wait_limit_ns;
+    return SWP_OK;
+}
+
+const char* swp_status_str(swp_status s)
+{
+    switch (s) {
+    case SWP_OK: return "SWP_OK";
+    case SWP_EINVAL: return "SWP_EINVAL";
+    case SWP_ENOMEM: return "SWP_ENOMEM";
+    case SWP_EBUDGET: return "SWP_EBUDGET";
+    case SWP_ECUDA: return "SWP_ECUDA";
+    case SWP_EUNSUPPORTED: return "SWP_EUNSUPPORTED";
+    case SWP_ETIMEOUT: return "SWP_ETIMEOUT";
+    case SWP_EDEVICE: return "SWP_EDEVICE";
+    }
+    return "SWP_UNKNOWN";
+}
+
+const char* swp_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernel
+// translation units (classic.cu, swept.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "scheme.cuh"
+
+namespace swp {
+
+// One sub-timestep of the classic decomposition over all N points (Section
+// 5.1): out = stage(src) with base values from `base` (KS / Euler).
+//   heat : src -> out                       (stage ignored)
+//   KS/Euler predictor (stage 0): src = base = u^m,      out = u^{m+1/2}
+//   KS/Euler final     (stage 1): src = u^{m+1/2}, base = u^m, out = u^m (in place)
+template <typename R>
+cudaError_t launch_classic(int eq, int bc, const R* src, const R* base, R* out, int64_t N,
+                           int stage, const Coefs<R>& c, int threads, cudaStream_t s);
+
+// Geometry of one swept phase (one kernel of the paper's Sections 4.2-4.3).
+struct PhaseGeom {
+    int64_t N;      // points
+    int n;          // node width (points per node)
+    int H;          // sub-timestep levels per half-cycle, n / (2 radius)
+    int K;          // nodes, N / n
+    int j_lo, j_hi; // levels computed, relative to the phase's base level
+    int odd;        // 1: nodes centred on node boundaries; 0: on node centres
+};
+
+// Shared memory a swept phase kernel needs for node width n.
+size_t swept_smem_bytes(int eq, int n, int elem_bytes);
+
+// One phase over all K nodes: every block loads its node's window of the two
+// level rows A (even levels) and B (odd levels), advances levels j_lo..j_hi in
+// shared memory and writes the window back.
+template <typename R>
+cudaError_t launch_swept_phase(int eq, int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
+                               int threads, cudaStream_t s);
+
+// Whole advance in one persistent launch: blocks claim (phase, node) items in
+// order and wait, with a bounded spin, for the two neighbouring nodes of the
+// previous phase.  flags[K] hold completed-phase counts offset by flag_base;
+// status != 0 after the kernel reports a wait that gave up.
+struct PersistentPlan {
+    int64_t N;
+    int n, H, K;
+    int64_t Q, r;          // full-height phases and remainder levels
+    int64_t n_phases;      // phases in this advance
+    uint32_t flag_base;    // flags already hold this many phases per node
+    uint32_t wait_offset;  // 0; a test hook sets it so that no wait can succeed
+    uint64_t wait_limit_ns;  // bound of one neighbour wait (device global timer)
+};
+
+template <typename R>
+cudaError_t launch_swept_persistent(int eq, int bc, R* A, R* B, const PersistentPlan& plan,
+                                    const Coefs<R>& c, uint32_t* flags, unsigned int* work_counter,
+                                    int* status, int threads, int blocks, cudaStream_t s);
+
+template <typename R>
+int swept_persistent_blocks_per_sm(int eq, int n, int threads);
+
+}  // namespace swp

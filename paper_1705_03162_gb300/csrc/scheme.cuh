@@ -1,0 +1,185 @@
+// Point updates of the three test problems (arXiv:1705.03162, Appendices
+// A-C), shared by the classic and the swept kernels so that both produce the
+// same bits.  Every operation is an explicit round-to-nearest intrinsic, so
+// the compiler neither contracts nor reorders: the rounding sequence is the
+// one written here.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace swp {
+
+enum Eq : int { HEAT = 0, KS = 1, EULER = 2 };
+enum Bc : int { PERIODIC = 0, REFLECTIVE = 1, DIRICHLET = 2 };
+
+// Round-to-nearest arithmetic in the working precision.
+template <typename R> struct Fp;
+template <> struct Fp<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+    static __device__ __forceinline__ double abs(double a) { return fabs(a); }
+};
+template <> struct Fp<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+    static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
+};
+
+// Per-problem constants, formed on the host in double and rounded once to R.
+template <typename R> struct Coefs {
+    R fo;                 // heat: Fourier number alpha dt / dx^2
+    R a1[2], a4[2], beta[2];  // KS stage s (0 predictor h = dt/2, 1 final h = dt):
+                          // a1 = -h/(4dx), a4 = -h/dx^4, beta = -h/dx^2 - 4 a4
+    R kh[2];              // Euler stage s: -(h/dx)/2 (G below is twice the flux)
+    R gm1, ggm1;          // gamma - 1, gamma (gamma - 1)
+    R ghost_l[3], ghost_r[3];  // Dirichlet end states, conserved
+};
+
+// ---------------------------------------------------------------------------
+// Heat, FTCS (Appendix A, Eq. heatdisc):
+//   T' = Fo (T_{i+1} + T_{i-1}) + (1 - 2 Fo) T_i = T_i + Fo (T_{i+1} - 2 T_i + T_{i-1})
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R heat_point(R tm, R t0, R tp, R fo)
+{
+    using F = Fp<R>;
+    R lap = F::fma(R(-2), t0, F::add(tp, tm));
+    return F::fma(fo, lap, t0);
+}
+
+// ---------------------------------------------------------------------------
+// Kuramoto-Sivashinsky, one midpoint-RK2 stage (Appendix B, Eqs. KSDisc, RKm,
+// RKf): out = base + h f(v), base = u^m, h = dt/2 (predictor) or dt (final).
+// The fourth difference v++ - 4v+ + 6v - 4v- + v-- equals d2 - 4 lap with
+// lap = v+ + v- - 2v and d2 = v++ + v-- - 2v, so
+//   h f = a1 (v+^2 - v-^2) + a4 d2 + beta lap.
+// Nine FP operations per stage.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R ks_point(R vmm, R vm, R v0, R vp, R vpp, R base,
+                                      R a1, R a4, R beta)
+{
+    using F = Fp<R>;
+    R b = F::fma(vp, vp, -F::mul(vm, vm));
+    R lap = F::fma(R(-2), v0, F::add(vp, vm));
+    R d2 = F::fma(R(-2), v0, F::add(vpp, vmm));
+    R acc = F::fma(a1, b, base);
+    acc = F::fma(a4, d2, acc);
+    return F::fma(beta, lap, acc);
+}
+
+// ---------------------------------------------------------------------------
+// Euler (Appendix C).  Conserved Q = (rho, rho u, E), E total energy per volume.
+// ---------------------------------------------------------------------------
+
+// Velocity and pressure, Eq. EulerP: u = (rho u)/rho, P = (gamma-1)(E - (rho u) u / 2).
+template <typename R>
+__device__ __forceinline__ R euler_pressure(R r, R m, R E, R gm1, R& u)
+{
+    using F = Fp<R>;
+    u = F::div(m, r);
+    return F::mul(gm1, F::fma(F::mul(R(-0.5), m), u, E));
+}
+
+// min(num/den, 1) for num, den nonzero with the same sign.  When
+// |num| >= |den| the quotient rounds to >= 1, so the division is skipped.
+template <typename R>
+__device__ __forceinline__ R limited_ratio(R num, R den)
+{
+    return (Fp<R>::abs(num) >= Fp<R>::abs(den)) ? R(1) : Fp<R>::div(num, den);
+}
+
+template <typename R>
+__device__ __forceinline__ bool same_sign(R a, R b)
+{
+    return (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
+}
+
+// Limited states at the interface between cells a (left) and b (right)
+// (Eqs. Pratio, limitleft, limitright): the ratio at cell a is
+// (pb - pa)/(pa - pam) and gives QL = Qa + min(ratio, 1)/2 (Qb - Qa) when it
+// lies in (0, inf); the inverse ratio at cell b, (pb - pa)/(pbp - pb), gives
+// QR = Qb + min(inverse, 1)/2 (Qa - Qb); otherwise first order.
+template <typename R>
+__device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], R pam, R pa,
+                                                  R pb, R pbp, R ql[3], R qr[3])
+{
+    using F = Fp<R>;
+    R num = F::sub(pb, pa), den = F::sub(pa, pam);
+    if (same_sign(num, den)) {
+        R h = F::mul(R(0.5), limited_ratio(num, den));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ql[c] = F::fma(h, F::sub(qb[c], qa[c]), qa[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ql[c] = qa[c];
+    }
+    R num2 = F::sub(pbp, pb);
+    if (same_sign(num2, num)) {
+        R h = F::mul(R(0.5), limited_ratio(num, num2));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qr[c] = F::fma(h, F::sub(qa[c], qb[c]), qb[c]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) qr[c] = qb[c];
+    }
+}
+
+// G = 2 Flux from the limited states: F(QR) + F(QL) + r_sp (QL - QR), with
+// F(Q) = (rho u, rho u^2 + P, u (E + P)) (Eq. EulerF) and spectral radius
+// r_sp = sqrt(gamma (gamma-1) (e_sp - u_sp^2/2)) + |u_sp| from sqrt(rho)-weighted
+// Roe averages of u and of e = E/rho (gamma P_sp / rho_sp with
+// P_sp = (gamma-1) rho_sp (e_sp - u_sp^2/2)).
+template <typename R>
+__device__ __forceinline__ void euler_flux(const R ql[3], const R qr[3], R gm1, R ggm1, R G[3])
+{
+    using F = Fp<R>;
+    R ul, ur;
+    R pl = euler_pressure(ql[0], ql[1], ql[2], gm1, ul);
+    R pr = euler_pressure(qr[0], qr[1], qr[2], gm1, ur);
+    R fl1 = F::fma(ql[1], ul, pl);
+    R fl2 = F::mul(ul, F::add(ql[2], pl));
+    R fr1 = F::fma(qr[1], ur, pr);
+    R fr2 = F::mul(ur, F::add(qr[2], pr));
+    R sl = F::sqrt(ql[0]);
+    R sr = F::sqrt(qr[0]);
+    R w = F::add(sl, sr);
+    R usp = F::div(F::fma(sl, ul, F::mul(sr, ur)), w);
+    R el = F::div(ql[2], ql[0]);
+    R er = F::div(qr[2], qr[0]);
+    R esp = F::div(F::fma(sl, el, F::mul(sr, er)), w);
+    R c2 = F::mul(ggm1, F::fma(F::mul(R(-0.5), usp), usp, esp));
+    R rsp = F::add(F::sqrt(c2), F::abs(usp));
+    G[0] = F::fma(rsp, F::sub(ql[0], qr[0]), F::add(qr[1], ql[1]));
+    G[1] = F::fma(rsp, F::sub(ql[1], qr[1]), F::add(fr1, fl1));
+    G[2] = F::fma(rsp, F::sub(ql[2], qr[2]), F::add(fr2, fl2));
+}
+
+// Interface value from the four cells around it and their pressures.
+template <typename R>
+__device__ __forceinline__ void euler_interface(const R qa[3], const R qb[3], R pam, R pa, R pb,
+                                                R pbp, R gm1, R ggm1, R G[3])
+{
+    R ql[3], qr[3];
+    euler_reconstruct(qa, qb, pam, pa, pb, pbp, ql, qr);
+    euler_flux(ql, qr, gm1, ggm1, G);
+}
+
+// Finite-volume RK2 stage: out = base - (h/dx)(Flux_{i+1/2} - Flux_{i-1/2})
+// = fma(kh, G_{i+1/2} - G_{i-1/2}, base).
+template <typename R>
+__device__ __forceinline__ R euler_update(R gp, R gm, R base, R kh)
+{
+    return Fp<R>::fma(kh, Fp<R>::sub(gp, gm), base);
+}
+
+}  // namespace swp

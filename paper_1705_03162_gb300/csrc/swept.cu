@@ -1,0 +1,466 @@
+// Swept time-space decomposition (arXiv:1705.03162 Sections 4.2-4.3) for
+// GB300.
+//
+// Geometry.  Nodes of n points, stencil radius rad (1 heat, 2 KS/Euler),
+// H = n / (2 rad) sub-timestep levels per half-cycle.  A phase is one kernel
+// of the paper: every node advances a space-time tile centred at x_c (node
+// centres in even phases, node boundaries in odd phases).  Relative to the
+// phase's base level the tile computes level j on the points
+// [x_c - w(j), x_c + w(j)) with w(j) = rad * min(j, 2H - j): levels 1..H grow
+// (inverted triangle), levels H+1..2H-1 shrink (upright triangle).  Phase 0 is
+// the upright triangle alone (levels H+1..2H-1 above the initial row); the
+// last phase is the closing inverted triangle (levels 1..H, or 1..r for a
+// final partial half-cycle, in which case the phase before it stops its
+// upright triangle at level H + r).
+//
+// Working set.  As in the paper, a node keeps two rows: even levels (heat
+// steps / RK2 final values) and odd levels (predictor values).  Each level's
+// outermost 2 rad values survive in these rows because even and odd levels'
+// edges never overlap (Fig. 2), and the two rows' surviving edges are exactly
+// what the neighbouring nodes of the next phase need.  Here the edges are
+// exchanged through two full-length rows in global memory, A (even levels)
+// and B (odd levels), at their absolute positions: a node loads its window
+// [x_c - n/2 - rad, x_c + n/2 + rad) of A and B into shared memory, runs its
+// levels with one barrier per level, and writes the window back.  Nodes of one
+// phase touch disjoint parts of A and B, so a phase needs no synchronisation
+// inside itself; a node of phase p depends only on its two overlapping nodes
+// of phase p-1.  At the end A (or B, when the last level is odd) holds the
+// full state.
+//
+// Boundaries.  Periodic problems wrap the window modulo N.  For reflective or
+// Dirichlet ends, the node straddling x = 0 (first node of odd phases, the
+// paper's split node) and the first/last nodes of even phases (whose widest
+// level reaches the ends) evaluate points next to a wall through a
+// boundary-aware gather.
+#include "launch.h"
+
+namespace swp {
+
+namespace {
+
+// Slot q of a node window stands for global point g0 + q (mod N).
+template <int EQ> struct Shape {
+    static constexpr int RAD = EQ == HEAT ? 1 : 2;
+    static constexpr int NV = EQ == EULER ? 3 : 1;
+};
+
+__host__ __device__ __forceinline__ int window_width(int n, int rad) { return n + 2 * rad; }
+
+__device__ __forceinline__ int64_t wrap(int64_t g, int64_t N)
+{
+    return g < 0 ? g + N : (g >= N ? g - N : g);
+}
+
+// Stencil value at slot q + d for the point at slot q, applying the boundary
+// condition when the stencil crosses a domain end: mirror about the end point
+// (u_{-k} = u_k, u_{N-1+k} = u_{N-1-k}) or the Dirichlet ghost state.
+template <typename R>
+__device__ __forceinline__ R wall_fetch(const R* row, int W, int q, int d, int v, int64_t g0,
+                                        int64_t N, int bc, const Coefs<R>& c)
+{
+    const int64_t gp = wrap(g0 + q, N);
+    const int64_t gt = gp + d;
+    if (gt < 0) {
+        if (bc == REFLECTIVE) return row[v * W + (int)(q - 2 * gp - d)];
+        return c.ghost_l[v];
+    }
+    if (gt >= N) {
+        if (bc == REFLECTIVE) return row[v * W + (int)(q + 2 * (N - 1 - gp) - d)];
+        return c.ghost_r[v];
+    }
+    return row[v * W + q + d];
+}
+
+// Load the node window of rows A / B (global, [NV][N]) into shared memory.
+// Row 0 (A) occupies slots [rad, rad + n); row 1 (B) all W slots.
+template <typename R, int EQ, bool CG>
+__device__ __forceinline__ void window_load(const R* A, const R* B, R* row0, R* row1, int n,
+                                            int64_t g0, int64_t N, bool need_b)
+{
+    constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
+    const int W = window_width(n, RAD);
+    for (int s = threadIdx.x; s < W; s += blockDim.x) {
+        const int64_t g = wrap(g0 + s, N);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (s >= RAD && s < RAD + n)
+                row0[v * W + s] = CG ? __ldcg(A + v * N + g) : A[v * N + g];
+            if (need_b) row1[v * W + s] = CG ? __ldcg(B + v * N + g) : B[v * N + g];
+        }
+    }
+}
+
+// Write back what the node may have changed: row 0 slots [rad, rad + n) and
+// row 1 slots [2 rad, n) (the odd levels of its upright triangle).
+template <typename R, int EQ, bool CG>
+__device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R* row1, int n,
+                                             int64_t g0, int64_t N)
+{
+    constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
+    const int W = window_width(n, RAD);
+    for (int s = threadIdx.x; s < W; s += blockDim.x) {
+        const int64_t g = wrap(g0 + s, N);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (s >= RAD && s < RAD + n) {
+                if (CG) __stcg(A + v * N + g, row0[v * W + s]);
+                else A[v * N + g] = row0[v * W + s];
+            }
+            if (s >= 2 * RAD && s < n) {
+                if (CG) __stcg(B + v * N + g, row1[v * W + s]);
+                else B[v * N + g] = row1[v * W + s];
+            }
+        }
+    }
+}
+
+// Advance levels j_lo..j_hi of one node in shared memory.
+//   row0 / row1 : [NV][W] even / odd level rows
+//   P, G        : Euler scratch, W pressures and [3][W + 1] interface values
+//   wall        : the node may evaluate points next to a non-periodic end
+template <typename R, int EQ>
+__device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n, int H, int j_lo,
+                                            int j_hi, int64_t g0, int64_t N, bool wall, int bc,
+                                            const Coefs<R>& c)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    const int W = window_width(n, RAD);
+    const int cs = n / 2 + RAD;
+    const int T = blockDim.x;
+    for (int j = j_lo; j <= j_hi; ++j) {
+        const int w = RAD * (j <= H ? j : 2 * H - j);
+        const int lo = cs - w, cnt = 2 * w;
+        R* dst = (j & 1) ? row1 : row0;
+        const R* src = (j & 1) ? row0 : row1;
+        const int stage = (EQ == HEAT) ? 0 : ((j & 1) ? 0 : 1);
+        if constexpr (EQ == HEAT) {
+            for (int t = threadIdx.x; t < cnt; t += T) {
+                const int q = lo + t;
+                R tm, tp;
+                if (wall) {
+                    tm = wall_fetch(src, W, q, -1, 0, g0, N, bc, c);
+                    tp = wall_fetch(src, W, q, 1, 0, g0, N, bc, c);
+                } else {
+                    tm = src[q - 1];
+                    tp = src[q + 1];
+                }
+                dst[q] = heat_point(tm, src[q], tp, c.fo);
+            }
+        } else if constexpr (EQ == KS) {
+            // KS problems are periodic: the window is already wrapped.
+            const R a1 = c.a1[stage], a4 = c.a4[stage], beta = c.beta[stage];
+            for (int t = threadIdx.x; t < cnt; t += T) {
+                const int q = lo + t;
+                const R base = stage == 0 ? src[q] : row0[q];
+                dst[q] = ks_point(src[q - 2], src[q - 1], src[q], src[q + 1], src[q + 2], base, a1,
+                                  a4, beta);
+            }
+        } else {
+            const R kh = c.kh[stage];
+            if (wall) {
+                // each cell gathers its five neighbours through the boundary
+                for (int t = threadIdx.x; t < cnt; t += T) {
+                    const int q = lo + t;
+                    R qs[5][3], p[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) {
+#pragma unroll
+                        for (int v = 0; v < 3; ++v)
+                            qs[k][v] = wall_fetch(src, W, q, k - 2, v, g0, N, bc, c);
+                        R u;
+                        p[k] = euler_pressure(qs[k][0], qs[k][1], qs[k][2], c.gm1, u);
+                    }
+                    R gm[3], gp[3];
+                    euler_interface(qs[1], qs[2], p[0], p[1], p[2], p[3], c.gm1, c.ggm1, gm);
+                    euler_interface(qs[2], qs[3], p[1], p[2], p[3], p[4], c.gm1, c.ggm1, gp);
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        const R base = stage == 0 ? src[v * W + q] : row0[v * W + q];
+                        dst[v * W + q] = euler_update(gp[v], gm[v], base, kh);
+                    }
+                }
+            } else {
+                // pressures of cells [lo-2, hi+2), interfaces [lo, hi], then cells
+                const int GW = W + 1;
+                for (int t = threadIdx.x; t < cnt + 4; t += T) {
+                    const int s = lo - 2 + t;
+                    R u;
+                    P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1, u);
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t <= cnt; t += T) {
+                    const int sb = lo + t;   // interface between slots sb-1 and sb
+                    R qa[3] = {src[sb - 1], src[W + sb - 1], src[2 * W + sb - 1]};
+                    R qb[3] = {src[sb], src[W + sb], src[2 * W + sb]};
+                    R g3[3];
+                    euler_interface(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], c.gm1, c.ggm1,
+                                    g3);
+                    G[sb] = g3[0];
+                    G[GW + sb] = g3[1];
+                    G[2 * GW + sb] = g3[2];
+                }
+                __syncthreads();
+                for (int t = threadIdx.x; t < cnt; t += T) {
+                    const int q = lo + t;
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        const R base = stage == 0 ? src[v * W + q] : row0[v * W + q];
+                        dst[v * W + q] = euler_update(G[v * GW + q + 1], G[v * GW + q], base, kh);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int EQ>
+__host__ __device__ __forceinline__ size_t smem_elems(int n)
+{
+    constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
+    const size_t W = (size_t)window_width(n, RAD);
+    size_t e = 2 * NV * W;
+    if (EQ == EULER) e += W + 3 * (W + 1);
+    return e;
+}
+
+template <typename R, int EQ>
+__device__ __forceinline__ void smem_rows(unsigned char* raw, int n, R*& row0, R*& row1, R*& P,
+                                          R*& G)
+{
+    constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
+    const int W = window_width(n, RAD);
+    R* sm = reinterpret_cast<R*>(raw);
+    row0 = sm;
+    row1 = sm + NV * W;
+    P = row1 + NV * W;
+    G = P + W;
+}
+
+// Which nodes may evaluate a point next to a non-periodic domain end: the
+// node centred on x = 0 and the first / last node of a phase.
+__device__ __forceinline__ bool node_near_wall(int bc, int k, int K)
+{
+    return bc != PERIODIC && (k == 0 || k == K - 1);
+}
+
+template <typename R, int EQ>
+__global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_phase_kernel(R* A, R* B, PhaseGeom g, int bc,
+                                                           Coefs<R> c)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *row0, *row1, *P, *G;
+    smem_rows<R, EQ>(smem_raw, g.n, row0, row1, P, G);
+    const int k = blockIdx.x;
+    const int64_t xc = g.odd ? (int64_t)k * g.n : (int64_t)k * g.n + g.n / 2;
+    const int64_t g0 = xc - g.n / 2 - RAD;
+    const bool need_b = g.j_lo <= g.H;   // every phase but the first reads odd-level edges
+    window_load<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N, need_b);
+    __syncthreads();
+    tile_levels<R, EQ>(row0, row1, P, G, g.n, g.H, g.j_lo, g.j_hi, g0, g.N,
+                       node_near_wall(bc, k, g.K), bc, c);
+    window_store<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: one launch for the whole advance.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p)
+{
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Hard cap on polls of one wait, in case the global timer does not advance.
+constexpr uint32_t kMaxPolls = 1u << 26;
+
+template <typename R, int EQ>
+__global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_kernel(R* A, R* B, PersistentPlan plan,
+                                                                int bc, Coefs<R> c,
+                                                                uint32_t* flags,
+                                                                unsigned int* counter, int* status)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ long long item_s;
+    __shared__ int abort_s;
+    R *row0, *row1, *P, *G;
+    smem_rows<R, EQ>(smem_raw, plan.n, row0, row1, P, G);
+    const int64_t total = plan.n_phases * plan.K;
+    const int H = plan.H, n = plan.n, K = plan.K;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            item_s = (long long)atomicAdd(counter, 1u);
+            abort_s = 0;
+        }
+        __syncthreads();
+        const int64_t item = item_s;
+        if (item >= total) break;
+        const int64_t p = item / K;
+        const int k = (int)(item - p * K);
+        const int odd = (int)(p & 1);
+        const int j_lo = p == 0 ? H + 1 : 1;
+        const int j_hi = p < plan.Q ? 2 * H - 1 : (p == plan.Q ? H + (int)plan.r : (int)plan.r);
+        if (p > 0 && threadIdx.x == 0) {
+            // the two nodes of phase p-1 whose windows overlap this one
+            const int kl = odd ? (k + K - 1) % K : k;
+            const int kr = odd ? k : (k + 1) % K;
+            const uint32_t need = plan.flag_base + (uint32_t)p + plan.wait_offset;
+            const uint64_t t_start = global_ns();
+            uint32_t polls = 0;
+            while ((int32_t)(ld_acquire(flags + kl) - need) < 0 ||
+                   (int32_t)(ld_acquire(flags + kr) - need) < 0) {
+                if (ld_volatile(status) != 0 || ++polls > kMaxPolls ||
+                    global_ns() - t_start > plan.wait_limit_ns) {
+                    atomicExch(status, 1);
+                    abort_s = 1;
+                    break;
+                }
+                __nanosleep(polls < 64 ? 32 : 256);
+            }
+        }
+        __syncthreads();
+        if (abort_s) break;
+        const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
+        const int64_t g0 = xc - n / 2 - RAD;
+        window_load<R, EQ, true>(A, B, row0, row1, n, g0, plan.N, j_lo <= H);
+        __syncthreads();
+        tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, plan.N,
+                           node_near_wall(bc, k, K), bc, c);
+        window_store<R, EQ, true>(A, B, row0, row1, n, g0, plan.N);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(flags + k, plan.flag_base + (uint32_t)p + 1);
+    }
+}
+
+template <typename R, int EQ>
+cudaError_t set_smem(const void* fn, size_t smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <typename R, int EQ>
+cudaError_t phase_launch_eq(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
+                            cudaStream_t s)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(g.n);
+    cudaError_t e = set_smem<R, EQ>((const void*)swept_phase_kernel<R, EQ>, smem);
+    if (e != cudaSuccess) return e;
+    swept_phase_kernel<R, EQ><<<g.K, threads, smem, s>>>(A, B, g, bc, c);
+    return cudaGetLastError();
+}
+
+template <typename R, int EQ>
+cudaError_t persistent_launch_eq(int bc, R* A, R* B, const PersistentPlan& plan, const Coefs<R>& c,
+                                 uint32_t* flags, unsigned int* counter, int* status, int threads,
+                                 int blocks, cudaStream_t s)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(plan.n);
+    cudaError_t e = set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ>, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    swept_persistent_kernel<R, EQ><<<blocks, threads, smem, s>>>(A, B, plan, bc, c, flags, counter,
+                                                                  status);
+    return cudaGetLastError();
+}
+
+template <typename R, int EQ>
+int persistent_bps_eq(int n, int threads)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(n);
+    if (set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ>, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_persistent_kernel<R, EQ>, threads,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+}  // namespace
+
+size_t swept_smem_bytes(int eq, int n, int elem_bytes)
+{
+    switch (eq) {
+    case HEAT: return (size_t)elem_bytes * smem_elems<HEAT>(n);
+    case KS: return (size_t)elem_bytes * smem_elems<KS>(n);
+    default: return (size_t)elem_bytes * smem_elems<EULER>(n);
+    }
+}
+
+template <typename R>
+cudaError_t launch_swept_phase(int eq, int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
+                               int threads, cudaStream_t s)
+{
+    switch (eq) {
+    case HEAT: return phase_launch_eq<R, HEAT>(bc, A, B, g, c, threads, s);
+    case KS: return phase_launch_eq<R, KS>(bc, A, B, g, c, threads, s);
+    default: return phase_launch_eq<R, EULER>(bc, A, B, g, c, threads, s);
+    }
+}
+
+template <typename R>
+cudaError_t launch_swept_persistent(int eq, int bc, R* A, R* B, const PersistentPlan& plan,
+                                    const Coefs<R>& c, uint32_t* flags, unsigned int* counter,
+                                    int* status, int threads, int blocks, cudaStream_t s)
+{
+    switch (eq) {
+    case HEAT:
+        return persistent_launch_eq<R, HEAT>(bc, A, B, plan, c, flags, counter, status, threads,
+                                             blocks, s);
+    case KS:
+        return persistent_launch_eq<R, KS>(bc, A, B, plan, c, flags, counter, status, threads,
+                                           blocks, s);
+    default:
+        return persistent_launch_eq<R, EULER>(bc, A, B, plan, c, flags, counter, status, threads,
+                                              blocks, s);
+    }
+}
+
+template <typename R>
+int swept_persistent_blocks_per_sm(int eq, int n, int threads)
+{
+    switch (eq) {
+    case HEAT: return persistent_bps_eq<R, HEAT>(n, threads);
+    case KS: return persistent_bps_eq<R, KS>(n, threads);
+    default: return persistent_bps_eq<R, EULER>(n, threads);
+    }
+}
+
+template cudaError_t launch_swept_phase<double>(int, int, double*, double*, const PhaseGeom&,
+                                                const Coefs<double>&, int, cudaStream_t);
+template cudaError_t launch_swept_phase<float>(int, int, float*, float*, const PhaseGeom&,
+                                               const Coefs<float>&, int, cudaStream_t);
+template cudaError_t launch_swept_persistent<double>(int, int, double*, double*,
+                                                     const PersistentPlan&, const Coefs<double>&,
+                                                     uint32_t*, unsigned int*, int*, int, int,
+                                                     cudaStream_t);
+template cudaError_t launch_swept_persistent<float>(int, int, float*, float*,
+                                                    const PersistentPlan&, const Coefs<float>&,
+                                                    uint32_t*, unsigned int*, int*, int, int,
+                                                    cudaStream_t);
+template int swept_persistent_blocks_per_sm<double>(int, int, int);
+template int swept_persistent_blocks_per_sm<float>(int, int, int);
+
+}  // namespace swp

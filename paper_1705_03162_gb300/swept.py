@@ -1,0 +1,242 @@
+"""Thin ctypes binding of libswept.so (C ABI in include/swept.h).
+
+Argument marshalling only: every step of the classic and swept schemes runs in
+the library's CUDA kernels.  Host buffers are numpy arrays; device buffers are
+CUDA torch tensors (torch provides device memory and streams).  A missing or
+unloadable library raises :class:`LibraryError`; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from .inputs import ProblemSpec
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libswept.so")
+
+OK, EINVAL, ENOMEM, EBUDGET, ECUDA, EUNSUPPORTED, ETIMEOUT, EDEVICE = range(8)
+HEAT, KS, EULER = 0, 1, 2
+PERIODIC, REFLECTIVE, DIRICHLET = 0, 1, 2
+F64, F32 = 0, 1
+CLASSIC, SWEPT = 0, 1
+LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT = 0, 1, 2
+
+_EQ = {"heat": HEAT, "ks": KS, "euler": EULER}
+_BC = {"periodic": PERIODIC, "reflective": REFLECTIVE, "dirichlet": DIRICHLET}
+_SCHEME = {"classic": CLASSIC, "swept": SWEPT}
+_LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT}
+_DTYPE = {"f64": F64, "f32": F32}
+
+# every symbol include/swept.h declares
+ABI_SYMBOLS = (
+    "swp_create", "swp_write", "swp_advance", "swp_advance_ex", "swp_read", "swp_synchronize",
+    "swp_destroy", "swp_shape", "swp_kernel_launches", "swp_required_bytes",
+    "swp_set_memory_budget", "swp_memory_in_use", "swp_debug_withhold_flags",
+    "swp_status_str", "swp_last_error",
+)
+
+
+class LibraryError(RuntimeError):
+    """libswept.so is missing or could not be loaded."""
+
+
+class SweptError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str):
+        super().__init__(f"{what}: {_status_name(status)}: {detail}")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("eq", ctypes.c_int32), ("bc", ctypes.c_int32), ("dtype", ctypes.c_int32),
+        ("reserved", ctypes.c_int32), ("n_points", ctypes.c_int64),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("left", ctypes.c_double * 3), ("right", ctypes.c_double * 3),
+    ]
+
+
+class AdvanceOpts(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("points_per_block", ctypes.c_int32),
+                ("launch", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libswept.so and declare its C signatures (raises LibraryError)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise LibraryError(f"{path} not found: build it with "
+                               "`python -m paper_1705_03162_gb300.build`")
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError as e:
+            raise LibraryError(f"cannot load {path}: {e}") from e
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        P = ctypes.c_void_p
+        sig = {
+            "swp_create": ([ctypes.POINTER(Desc), vp, ctypes.c_int, vp, ctypes.POINTER(P)], ctypes.c_int),
+            "swp_write": ([P, vp, sz, ctypes.c_int], ctypes.c_int),
+            "swp_advance": ([P, i64, i32, i32], ctypes.c_int),
+            "swp_advance_ex": ([P, i64, ctypes.POINTER(AdvanceOpts)], ctypes.c_int),
+            "swp_read": ([P, vp, sz, ctypes.c_int], ctypes.c_int),
+            "swp_synchronize": ([P], ctypes.c_int),
+            "swp_destroy": ([P], ctypes.c_int),
+            "swp_shape": ([P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_kernel_launches": ([P], i64),
+            "swp_required_bytes": ([ctypes.POINTER(Desc), ctypes.POINTER(sz)], ctypes.c_int),
+            "swp_set_memory_budget": ([sz], ctypes.c_int),
+            "swp_memory_in_use": ([], sz),
+            "swp_debug_withhold_flags": ([P, ctypes.c_int, i64], ctypes.c_int),
+            "swp_status_str": ([ctypes.c_int], ctypes.c_char_p),
+            "swp_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["SWP_OK", "SWP_EINVAL", "SWP_ENOMEM", "SWP_EBUDGET", "SWP_ECUDA",
+             "SWP_EUNSUPPORTED", "SWP_ETIMEOUT", "SWP_EDEVICE"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise SweptError(status, what, load_library().swp_last_error().decode())
+
+
+def make_desc(spec: ProblemSpec, dtype: str = "f64") -> Desc:
+    d = Desc()
+    d.eq, d.bc, d.dtype, d.reserved = _EQ[spec.eq], _BC[spec.bc], _DTYPE[dtype], 0
+    d.n_points, d.dx, d.dt = spec.n_points, spec.dx, spec.dt
+    d.alpha, d.gamma = spec.alpha, spec.gamma
+    d.left = (ctypes.c_double * 3)(*spec.left)
+    d.right = (ctypes.c_double * 3)(*spec.right)
+    return d
+
+
+def _buffer(x):
+    """(pointer, bytes, on_device) of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, x.nbytes, 0
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        nbytes = x.numel() * x.element_size()
+        if x.is_cuda:
+            return x.data_ptr(), nbytes, 1
+        return x.data_ptr(), nbytes, 0
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def required_bytes(spec: ProblemSpec, dtype: str = "f64") -> int:
+    lib = load_library()
+    out = ctypes.c_size_t(0)
+    _check(lib.swp_required_bytes(ctypes.byref(make_desc(spec, dtype)), ctypes.byref(out)), "required_bytes")
+    return out.value
+
+
+def set_memory_budget(nbytes: int):
+    _check(load_library().swp_set_memory_budget(int(nbytes)), "set_memory_budget")
+
+
+def memory_in_use() -> int:
+    return int(load_library().swp_memory_in_use())
+
+
+class Problem:
+    """One 1D problem whose state lives in the library's device memory.
+
+    ``u0`` is a numpy array (host) or CUDA tensor (device) of shape (nv, N) in
+    the problem's dtype; ``stream`` is a ``torch.cuda.Stream`` (or raw
+    cudaStream_t handle) or None for the default stream.
+    """
+
+    def __init__(self, spec: ProblemSpec, u0, dtype: str = "f64", stream=None):
+        self._lib = load_library()
+        self.spec, self.dtype = spec, dtype
+        self.nv, self.n_points = spec.nv, spec.n_points
+        self.np_dtype = np.float64 if dtype == "f64" else np.float32
+        self._h = ctypes.c_void_p(0)
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
+        ptr, nbytes, dev = _buffer(u0)
+        if nbytes != self.nbytes:
+            raise ValueError(f"u0 has {nbytes} bytes, expected {self.nbytes}")
+        self._desc = make_desc(spec, dtype)
+        _check(self._lib.swp_create(ctypes.byref(self._desc), ctypes.c_void_p(ptr), dev,
+                                    ctypes.c_void_p(handle), ctypes.byref(self._h)), "create")
+
+    @property
+    def nbytes(self) -> int:
+        return self.nv * self.n_points * (8 if self.dtype == "f64" else 4)
+
+    def advance(self, steps: int, scheme: str = "swept", n: int = 0, launch: str = "auto",
+                threads: int = 0):
+        o = AdvanceOpts(_SCHEME[scheme], int(n), _LAUNCH[launch], int(threads))
+        _check(self._lib.swp_advance_ex(self._h, int(steps), ctypes.byref(o)), "advance")
+        return self
+
+    def read(self, out=None):
+        """Copy the state into ``out`` (numpy or CUDA tensor) or a new numpy array."""
+        if out is None:
+            out = np.empty((self.nv, self.n_points), dtype=self.np_dtype)
+        ptr, nbytes, dev = _buffer(out)
+        _check(self._lib.swp_read(self._h, ctypes.c_void_p(ptr), nbytes, dev), "read")
+        return out
+
+    def write(self, src):
+        ptr, nbytes, dev = _buffer(src)
+        _check(self._lib.swp_write(self._h, ctypes.c_void_p(ptr), nbytes, dev), "write")
+
+    def synchronize(self):
+        _check(self._lib.swp_synchronize(self._h), "synchronize")
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.swp_kernel_launches(self._h))
+
+    def debug_withhold_flags(self, withhold: bool, wait_limit_ns: int = 2_000_000_000):
+        _check(self._lib.swp_debug_withhold_flags(self._h, int(bool(withhold)), int(wait_limit_ns)),
+               "debug_withhold_flags")
+
+    def close(self):
+        if self._h and self._h.value:
+            _check(self._lib.swp_destroy(self._h), "destroy")
+            self._h = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(spec: ProblemSpec, u0: np.ndarray, steps: int, scheme: str = "swept", n: int = 0,
+          dtype: Optional[str] = None, launch: str = "auto", threads: int = 0) -> np.ndarray:
+    """Create, advance ``steps`` timesteps and read back (host arrays)."""
+    dtype = dtype or ("f32" if u0.dtype == np.float32 else "f64")
+    with Problem(spec, np.ascontiguousarray(u0), dtype) as p:
+        p.advance(steps, scheme, n, launch, threads)
+        return p.read()

@@ -1,0 +1,99 @@
+"""The C-ABI library builds, loads and exports every symbol include/swept.h
+declares; host-side argument checks.  CPU only: no kernel runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1705_03162_gb300 import build as B
+from paper_1705_03162_gb300 import inputs as I
+from paper_1705_03162_gb300 import swept as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load_library()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "swept.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(swp_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_binding_symbols():
+    assert sorted(S.ABI_SYMBOLS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    assert lib.swp_status_str(S.OK) == b"SWP_OK"
+    assert lib.swp_status_str(S.ETIMEOUT) == b"SWP_ETIMEOUT"
+
+
+def _create(lib, desc):
+    h = ctypes.c_void_p(0)
+    buf = (ctypes.c_double * 16)()
+    return lib.swp_create(ctypes.byref(desc), buf, 0, None, ctypes.byref(h)), h
+
+
+def test_create_rejects_bad_descriptions(lib):
+    d = S.make_desc(I.ks_spec(64))
+    d.eq = 7
+    assert _create(lib, d)[0] == S.EINVAL
+    d = S.make_desc(I.ks_spec(64))
+    d.bc = S.REFLECTIVE
+    assert _create(lib, d)[0] == S.EUNSUPPORTED
+    d = S.make_desc(I.sod_spec(64), "f32")
+    assert _create(lib, d)[0] == S.EUNSUPPORTED
+    d = S.make_desc(I.heat_spec(64))
+    d.dt = float("nan")
+    assert _create(lib, d)[0] == S.EINVAL
+    d = S.make_desc(I.heat_spec(64))
+    d.n_points = 3
+    assert _create(lib, d)[0] == S.EINVAL
+    d = S.make_desc(I.heat_spec(64))
+    d.reserved = 1
+    assert _create(lib, d)[0] == S.EINVAL
+    assert b"reserved" in lib.swp_last_error()
+
+
+def test_create_null_arguments(lib):
+    d = S.make_desc(I.heat_spec(64))
+    assert lib.swp_create(ctypes.byref(d), None, 0, None, ctypes.byref(ctypes.c_void_p())) == S.EINVAL
+    assert lib.swp_create(ctypes.byref(d), ctypes.c_void_p(1), 0, None, None) == S.EINVAL
+
+
+def test_null_handles(lib):
+    assert lib.swp_destroy(None) == S.OK
+    assert lib.swp_advance(None, 1, S.SWEPT, 0) == S.EINVAL
+    assert lib.swp_read(None, None, 0, 0) == S.EINVAL
+    assert lib.swp_synchronize(None) == S.EINVAL
+    assert lib.swp_kernel_launches(None) == -1
+
+
+def test_required_bytes_and_budget(lib):
+    assert S.required_bytes(I.sod_spec(1024)) == 2 * 3 * 1024 * 8
+    assert S.required_bytes(I.heat_spec(1024), "f32") == 2 * 1024 * 4
+    S.set_memory_budget(1000)
+    try:
+        d = S.make_desc(I.heat_spec(1024))
+        st, _ = _create(lib, d)
+        assert st == S.EBUDGET
+        assert S.memory_in_use() == 0
+    finally:
+        S.set_memory_budget(0)
+
+
+def test_missing_library_raises(tmp_path, monkeypatch):
+    monkeypatch.setattr(S, "_lib", None)
+    with pytest.raises(S.LibraryError):
+        S.load_library(str(tmp_path / "nope.so"))

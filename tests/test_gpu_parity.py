@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA classic and swept paths against the CPU oracle, element
+by element on the same seeded inputs, and against each other bit for bit.
+
+Tolerances (relative max-norm per variable): 1e-12 for FP64, 1e-5 for FP32
+(against the oracle run in the same precision).  Both CUDA paths evaluate the
+same device point update with explicit round-to-nearest operations in the
+oracle's order, so they are also checked to be bit-identical to the oracle.
+Sizes span several classic tiles (512 points) and several swept nodes with a
+ragged tail; step counts leave remainders of the swept half-cycle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from helpers import oprob, rel_max, spec_for, state_for
+from paper_1705_03162_gb300 import build as B
+from paper_1705_03162_gb300 import inputs as I
+from paper_1705_03162_gb300 import swept as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    S.load_library()
+
+
+def _np(dtype):
+    return np.float64 if dtype == "f64" else np.float32
+
+
+def _gpu(spec, u0, steps, dtype, scheme, n=0, launch="per_phase"):
+    with S.Problem(spec, u0, dtype) as p:
+        p.advance(steps, scheme, n, launch)
+        return p.read()
+
+
+def _oracle(spec, u0, steps):
+    ref = u0.copy()
+    O.classic(oprob(spec), ref, steps)
+    return ref
+
+
+CASES = [
+    # eq, bc, N, dtype, steps, node widths
+    ("heat", "periodic", 4992, "f64", 203, (32, 64, 128)),
+    ("heat", "reflective", 4992, "f64", 157, (32, 64, 128)),
+    ("heat", "periodic", 4992, "f32", 203, (32, 128)),
+    ("heat", "reflective", 4992, "f32", 90, (64,)),
+    ("ks", "periodic", 4992, "f64", 301, (32, 96, 128)),
+    ("ks", "periodic", 4992, "f32", 301, (64, 128)),
+    ("euler", "dirichlet", 4992, "f64", 333, (32, 64, 128)),
+    ("euler", "periodic", 4992, "f64", 211, (32, 104)),
+]
+
+
+@pytest.mark.parametrize("eq,bc,N,dtype,steps,widths", CASES)
+def test_classic_matches_oracle(eq, bc, N, dtype, steps, widths):
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec, _np(dtype))
+    ref = _oracle(spec, u0, steps)
+    got = _gpu(spec, u0, steps, dtype, "classic")
+    assert rel_max(got, ref) <= TOL[dtype]
+    assert np.array_equal(got, ref), "classic is not bit-identical to the oracle"
+
+
+@pytest.mark.parametrize("eq,bc,N,dtype,steps,widths", CASES)
+@pytest.mark.parametrize("launch", ["per_phase", "persistent"])
+def test_swept_matches_oracle_and_classic(eq, bc, N, dtype, steps, widths, launch):
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec, _np(dtype))
+    ref = _oracle(spec, u0, steps)
+    classic = _gpu(spec, u0, steps, dtype, "classic")
+    for n in widths:
+        got = _gpu(spec, u0, steps, dtype, "swept", n, launch)
+        assert rel_max(got, ref) <= TOL[dtype], f"n={n}"
+        assert np.array_equal(got, classic), f"swept != classic bitwise at n={n}"
+
+
+@pytest.mark.parametrize("eq,bc", [("heat", "periodic"), ("heat", "reflective"), ("ks", "periodic"),
+                                   ("euler", "dirichlet")])
+@pytest.mark.parametrize("steps", [0, 1, 2, 5, 16, 17, 33])
+def test_swept_short_and_ragged_advances(eq, bc, steps):
+    N, n = 512, 64
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec)
+    ref = _oracle(spec, u0, steps)
+    for launch in ("per_phase", "persistent"):
+        got = _gpu(spec, u0, steps, "f64", "swept", n, launch)
+        assert np.array_equal(got, ref), (launch, steps)
+
+
+@pytest.mark.parametrize("eq,bc,N,n", [
+    ("ks", "periodic", 256, 256),        # a single node
+    ("ks", "periodic", 512, 256),        # two nodes
+    ("heat", "periodic", 128, 128),
+    ("heat", "reflective", 256, 128),
+    ("euler", "dirichlet", 256, 128),
+    ("ks", "periodic", 65536, 8192),     # widest KS node in shared memory
+    ("heat", "periodic", 65536, 8192),
+    ("euler", "dirichlet", 16384, 2048),
+])
+def test_swept_node_count_extremes(eq, bc, N, n):
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec)
+    steps = 3 * n // (2 * spec.radius * spec.substeps) + 5
+    steps = min(steps, 700)
+    ref = _oracle(spec, u0, steps)
+    for launch in ("per_phase", "persistent"):
+        got = _gpu(spec, u0, steps, "f64", "swept", n, launch)
+        assert np.array_equal(got, ref), launch
+
+
+@pytest.mark.parametrize("launch", ["per_phase", "persistent"])
+def test_split_advances_equal_one_advance(launch):
+    """The state is complete after every advance (closing triangle), so
+    advancing a then b steps equals advancing a + b (checkpoint / resume)."""
+    spec = spec_for("ks", "periodic", 2048)
+    u0 = state_for(spec)
+    with S.Problem(spec, u0) as p:
+        p.advance(37, "swept", 128, launch)
+        mid = p.read()
+        p.advance(85, "swept", 64, launch)
+        end = p.read()
+    with S.Problem(spec, mid) as q:
+        q.advance(85, "classic")
+        end2 = q.read()
+    assert np.array_equal(mid, _oracle(spec, u0, 37))
+    assert np.array_equal(end, end2)
+
+
+def test_heat_config_closed_form_and_oracle():
+    """Heat configuration: N = 1024, r = 0.25, 4096 steps, 64 points per node."""
+    spec = I.heat_spec(1024, r=0.25)
+    u0 = I.initial_state(spec)
+    ref = _oracle(spec, u0, 4096)
+    for launch in ("per_phase", "persistent"):
+        got = _gpu(spec, u0, 4096, "f64", "swept", 64, launch)
+        assert np.array_equal(got, ref)
+    x = np.arange(1024) / 1024
+    G = lambda k: 1.0 - np.sin(np.pi * k / 1024) ** 2
+    exact = np.sin(2 * np.pi * x) * G(1) ** 4096
+    for k, a in zip(range(2, 10), I.heat_mode_amplitudes()):
+        exact += a * np.sin(2 * np.pi * k * x) * G(k) ** 4096
+    assert rel_max(got[0], exact) < 1e-11
+
+
+def test_sod_full_time_against_oracle():
+    """Sod tube to t = 0.2 (N steps at dt/dx = 0.2), N = 2^12."""
+    N = 4096
+    spec = I.sod_spec(N)
+    u0 = I.initial_state(spec)
+    ref = _oracle(spec, u0, N)
+    got_c = _gpu(spec, u0, N, "f64", "classic")
+    got_s = _gpu(spec, u0, N, "f64", "swept", 256, "persistent")
+    assert rel_max(got_c, ref) <= 1e-12 and rel_max(got_s, ref) <= 1e-12
+    assert np.array_equal(got_s, got_c)
+
+
+def test_invalid_node_width_rejected():
+    spec = spec_for("ks", "periodic", 1000)
+    with S.Problem(spec, state_for(spec)) as p:
+        for n in (12, 48 + 4, 2000, 1 << 20):
+            with pytest.raises(S.SweptError) as e:
+                p.advance(10, "swept", n)
+            assert e.value.status == S.EINVAL
+
+
+def test_device_buffers_roundtrip():
+    torch = pytest.importorskip("torch")
+    spec = spec_for("ks", "periodic", 4096)
+    u0 = state_for(spec)
+    dev = torch.from_numpy(u0).cuda()
+    s = torch.cuda.Stream()
+    with S.Problem(spec, dev, stream=s) as p:
+        p.advance(50, "swept", 256)
+        out = torch.empty_like(dev)
+        p.read(out)
+        s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), _oracle(spec, u0, 50))
