@@ -49,7 +49,11 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
 # a hash of the kernel sources it was taken on; reported as null once the
 # sources change.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/swept_phase_kernel_ks_n512.md: dram__bytes_read.sum + dram__bytes_write.sum of a
+    # full-diamond launch (16.78 MB + 0), cold caches
+    "swept_phase_kernel<double,KS> n=512": {"src": "cc59ea96f376ed8e", "bytes_per_launch": 16784384},
+}
 
 
 def _kernel_src_hash() -> str:
