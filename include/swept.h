@@ -163,6 +163,30 @@ size_t swp_memory_in_use(void);
  * kernel boundaries (Section 3). */
 swp_status swp_debug_withhold_flags(swp_problem* p, int withhold, int64_t wait_limit_ns);
 
+/* Swept advance that allocates nothing.  The paper has no counterpart: it is
+ * here for callers that cannot call cudaMalloc -- code whose device memory is
+ * owned by a pool or arena, loops that forbid allocation once running, or
+ * hosts that hand the library only pre-allocated buffers.
+ *   desc             : problem description (as for swp_create)
+ *   state            : DEVICE buffer of nv * N values ([nv][N], the dtype),
+ *                      read as the initial state and overwritten with the
+ *                      state after n_steps timesteps; owned by the caller
+ *   points_per_block : node width as for swp_advance (0 = auto)
+ *   threads          : threads per block (0 = auto)
+ *   cuda_stream      : stream for the work (NULL = legacy default stream)
+ * The swept scheme's scratch (its odd-level row) is a fixed 8 MiB array built
+ * into the library, so the state may hold at most 8 MiB (for example 2^20
+ * FP64 points); larger states fail with SWP_EINVAL.  Every GPU that loads the
+ * library holds that array until the process exits.  The first call on a
+ * device looks up the array's device address (set-up, once per device, with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the one array, so calls whose GPU work overlaps (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * No scratch value is read before the call writes it, so nothing needs
+ * clearing between calls.  Asynchronous on cuda_stream; no synchronisation. */
+swp_status swp_swept_noalloc(const swp_desc* desc, void* state, int64_t n_steps,
+                             int32_t points_per_block, int32_t threads, void* cuda_stream);
+
 const char* swp_status_str(swp_status s);
 const char* swp_last_error(void);
 

@@ -4,6 +4,7 @@
 // Built with host FP contraction off so the coefficients below round exactly
 // as written.
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -543,3 +544,99 @@ const char* swp_status_str(swp_status s)
 const char* swp_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Swept advance without allocation.
+//
+// Some callers cannot call cudaMalloc: code running inside a memory pool or
+// arena that owns all device memory, real-time loops that forbid allocation
+// after start-up, or host environments that hand the library only
+// pre-allocated device buffers.  swp_swept_noalloc serves them: the caller
+// passes the state buffer, and the swept scheme's one piece of scratch, the
+// odd-level row, lives in the file-scope array below.  It is sized for at
+// most kNoAllocScratchBytes of state (8 MiB: 2^20 FP64 values), and every
+// GPU that loads this library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device `dev`, looked up
+// once per device.  In host code the array's name only stands in for the
+// symbol; the kernel must be given this address.
+swp_status noalloc_scratch(int dev, void** out)
+{
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SWP_EDEVICE, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_fail(e, "scratch symbol address");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SWP_OK;
+}
+
+}  // namespace
+
+extern "C" swp_status swp_swept_noalloc(const swp_desc* desc, void* state, int64_t n_steps,
+                                        int32_t points_per_block, int32_t threads, void* cuda_stream)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!state) return fail(SWP_EINVAL, "state is NULL");
+    if (n_steps < 0 || n_steps > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps out of range");
+    const size_t sbytes = state_bytes(desc);
+    if (sbytes > kNoAllocScratchBytes)
+        return fail(SWP_EINVAL, "state of %zu bytes exceeds the %zu-byte scratch of swp_swept_noalloc; "
+                    "use swp_create / swp_advance for larger problems", sbytes, kNoAllocScratchBytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(SWP_EDEVICE, "libswept is built for sm_103 (device is sm_%d%d)", prop.major, prop.minor);
+    void* scratch = nullptr;
+    st = noalloc_scratch(dev, &scratch);
+    if (st != SWP_OK) return st;
+    if (n_steps == 0) return SWP_OK;
+
+    // a problem record on the stack whose two level rows are the caller's
+    // state (even levels) and the scratch array (odd levels)
+    swp_problem p;
+    p.desc = *desc;
+    p.nv = nv_of(desc->eq);
+    p.rad = radius_of(desc->eq);
+    p.sub = desc->eq == SWP_HEAT ? 1 : 2;
+    p.esize = esize_of(desc->dtype);
+    p.N = desc->n_points;
+    p.rows[0] = state;
+    p.rows[1] = scratch;
+    p.cur = 0;
+    p.stream = (cudaStream_t)cuda_stream;
+    p.device = dev;
+    p.sms = prop.multiProcessorCount;
+    make_coefs<double>(desc, p.cd);
+    make_coefs<float>(desc, p.cf);
+    swp_advance_opts o;
+    o.scheme = SWP_SWEPT;
+    o.points_per_block = points_per_block;
+    o.launch = SWP_LAUNCH_PER_PHASE;
+    o.threads = threads;
+    st = desc->dtype == SWP_F64 ? advance_typed<double>(&p, n_steps, o) : advance_typed<float>(&p, n_steps, o);
+    if (st != SWP_OK) return st;
+    if (p.cur == 1) {
+        // the last level was odd: the result sits in the scratch row
+        e = cudaMemcpyAsync(state, scratch, sbytes, cudaMemcpyDeviceToDevice, p.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "result copy from scratch");
+    }
+    return SWP_OK;
+}

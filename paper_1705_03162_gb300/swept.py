@@ -37,7 +37,7 @@ ABI_SYMBOLS = (
     "swp_create", "swp_write", "swp_advance", "swp_advance_ex", "swp_read", "swp_synchronize",
     "swp_destroy", "swp_shape", "swp_kernel_launches", "swp_required_bytes",
     "swp_set_memory_budget", "swp_memory_in_use", "swp_debug_withhold_flags",
-    "swp_status_str", "swp_last_error",
+    "swp_status_str", "swp_last_error", "swp_swept_noalloc",
 )
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
             "swp_set_memory_budget": ([sz], ctypes.c_int),
             "swp_memory_in_use": ([], sz),
             "swp_debug_withhold_flags": ([P, ctypes.c_int, i64], ctypes.c_int),
+            "swp_swept_noalloc": ([ctypes.POINTER(Desc), vp, i64, i32, i32, vp], ctypes.c_int),
             "swp_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "swp_last_error": ([], ctypes.c_char_p),
         }
@@ -240,3 +241,20 @@ def solve(spec: ProblemSpec, u0: np.ndarray, steps: int, scheme: str = "swept", 
     with Problem(spec, np.ascontiguousarray(u0), dtype) as p:
         p.advance(steps, scheme, n, launch, threads)
         return p.read()
+
+
+def swept_noalloc(spec: ProblemSpec, state, steps: int, n: int = 0, threads: int = 0,
+                  stream=None, dtype: str = "f64"):
+    """Advance the CUDA tensor ``state`` (shape (nv, N)) in place by ``steps``
+    timesteps with the swept scheme through swp_swept_noalloc, which allocates
+    no device memory (its scratch is a fixed 8 MiB array inside the library).
+    Asynchronous on ``stream``; calls that overlap on the GPU race."""
+    lib = load_library()
+    ptr, nbytes, dev = _buffer(state)
+    if not dev:
+        raise ValueError("state must be a CUDA tensor")
+    desc = make_desc(spec, dtype)
+    handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
+    _check(lib.swp_swept_noalloc(ctypes.byref(desc), ctypes.c_void_p(ptr), int(steps), int(n),
+                                 int(threads), ctypes.c_void_p(handle)), "swept_noalloc")
+    return state
