@@ -38,10 +38,10 @@ DEFAULT_WORKLOAD = {
 METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served solve latency"
 UNIT = "G point-updates/s"
 
-# Floating-point operations of one KS point-update (two RK2 stages of nine
-# FP64 operations: six FMAs, two adds, one multiply = 15 flops each).
-KS_FLOPS_PER_UPDATE = 30
-KS_FP64_OPS_PER_UPDATE = 18
+# Floating-point operations of one KS point-update (two RK2 stages of eight
+# FP64 operations: five FMAs, two adds, one multiply = 13 flops each).
+KS_FLOPS_PER_UPDATE = 26
+KS_FP64_OPS_PER_UPDATE = 16
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal
 # 1.25 TFLOP/s dense FP64 at the maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12

@@ -151,6 +151,44 @@ swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes);
 swp_status swp_set_memory_budget(size_t bytes);
 size_t swp_memory_in_use(void);
 
+/* ---- Batched swept advance (many independent problems, one launch) ----
+ * Advancing many small problems one by one leaves most of the GPU idle and
+ * pays a launch per phase each.  A batch advances every problem given to it
+ * in one persistent launch per (equation, dtype) group: work is a table of
+ * (problem, phase) tasks in phase-major order; each block claims one node of
+ * the current task at a time and waits, bounded, for the problem's two
+ * neighbouring nodes of the previous phase (the paper's kernel-boundary
+ * synchronisation of Section 3, done per node instead of per grid).  Each
+ * problem's result is bit-identical to swp_advance with the same node width.
+ * The paper has no batched form. */
+typedef struct swp_batch swp_batch;
+
+/* A batch runs its work on cuda_stream (NULL = legacy default stream); every
+ * problem given to it must have been created with that stream. */
+swp_status swp_batch_create(void* cuda_stream, swp_batch** out);
+
+/* Advance problems[i] by n_steps[i] timesteps (swept), i < count.
+ * points_per_block: per-problem node widths, or NULL / 0 entries for the
+ * tuned width of swp_autotune_width (else the default rule).  threads: block
+ * size (0 = 256; Euler at most 256).  Problems must be distinct.  Asynchronous;
+ * SWP_ETIMEOUT surfaces at swp_batch_synchronize. */
+swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
+                             int32_t count, const int32_t* points_per_block, int32_t threads);
+swp_status swp_batch_synchronize(swp_batch* b);
+swp_status swp_batch_destroy(swp_batch* b);
+int64_t swp_batch_kernel_launches(const swp_batch* b);
+
+/* Node-width autotuner.  Times batch_count copies of the problem (initial
+ * state u0_host, host memory) advanced `steps` timesteps in one batch for
+ * every power-of-two node width that fits, keeps the fastest for the
+ * (equation, dtype, n_points) of desc, and returns it in best_n.  Later
+ * batches use it for problems of that key.  Allocates and frees its own
+ * trial problems; synchronises the device. */
+swp_status swp_autotune_width(const swp_desc* desc, const void* u0_host, int32_t batch_count,
+                              int64_t steps, int32_t* best_n);
+/* The tuned width for desc's (equation, dtype, n_points), or 0 if none. */
+swp_status swp_tuned_width(const swp_desc* desc, int32_t* n);
+
 /* Fault-injection hook for tests of the persistent launch's bounded waits.
  * withhold != 0 makes every neighbour wait of later SWP_LAUNCH_PERSISTENT
  * advances of this problem wait for a flag value no node ever publishes, so

@@ -3,8 +3,12 @@
 // swept (triangle / diamond / closing phases, Sections 4.2-4.3) schemes.
 // Built with host FP contraction off so the coefficients below round exactly
 // as written.
+#include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -110,6 +114,7 @@ void make_coefs(const swp_desc* d, Coefs<R>& c)
         c.a1[s] = (R)a1;
         c.a4[s] = (R)a4;
         c.beta[s] = (R)(a2 - 4.0 * a4);
+        c.gam[s] = (R)(6.0 * a4 - 2.0 * a2);
         const double lam = d->dt / d->dx;
         const double lamh = s == 0 ? 0.5 * lam : lam;
         c.kh[s] = (R)(-(0.5 * lamh));
@@ -279,7 +284,10 @@ swp_status run_swept_persistent(swp_problem* p, const SweptPlan& s, int threads)
     if (total >= ((int64_t)1 << 31)) return fail(SWP_EINVAL, "advance too long for one persistent launch");
     const int bps = swept_persistent_blocks_per_sm<R>(p->desc.eq, s.n, threads);
     if (bps <= 0) return fail(SWP_EINVAL, "persistent kernel does not fit (n=%d, threads=%d)", s.n, threads);
+    // enough blocks for about two phases in flight: more would only poll the
+    // flags of phases that cannot start yet
     int64_t blocks = (int64_t)p->sms * bps;
+    if (blocks > 2 * (int64_t)s.K) blocks = 2 * (int64_t)s.K > p->sms ? 2 * (int64_t)s.K : p->sms;
     if (blocks > total) blocks = total;
     PersistentPlan plan;
     plan.N = p->N;
@@ -542,6 +550,304 @@ const char* swp_status_str(swp_status s)
 }
 
 const char* swp_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched swept advance and node-width autotuner.
+// ---------------------------------------------------------------------------
+struct swp_batch {
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 0;
+    int64_t launches = 0;
+    // device workspace, grown on demand
+    void* insts = nullptr;   size_t insts_cap = 0;
+    int2* tasks = nullptr;   size_t tasks_cap = 0;
+    int* ctr = nullptr;      size_t ctr_cap = 0;     // [0] = cur_task, [1] = status, [2..] = task counters
+    uint32_t* flags = nullptr; size_t flags_cap = 0;
+    uint64_t wait_limit_ns = 2000000000ull;
+};
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int64_t>, int> g_tuned;   // (eq, dtype, N) -> node width
+
+swp_status grow(void** p, size_t* cap, size_t bytes)
+{
+    if (*cap >= bytes) return SWP_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t want = bytes + bytes / 2 + 256;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) return fail(SWP_ENOMEM, "batch workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+    *cap = want;
+    return SWP_OK;
+}
+
+// Node width for a problem: the tuned value for (eq, dtype, N) if the tuner
+// measured one, else the default rule.
+int width_for(const swp_problem* p)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(std::make_tuple(p->desc.eq, p->desc.dtype, p->N));
+        if (it != g_tuned.end() && check_width(p, it->second) == SWP_OK) return it->second;
+    }
+    return default_width(p);
+}
+
+struct BatchItem {
+    swp_problem* p;
+    SweptPlan s;
+};
+
+template <typename R>
+swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int eq, int threads)
+{
+    std::vector<BatchInst<R>> insts(items.size());
+    int64_t flags = 0, max_phases = 0;
+    int max_n = 0;
+    for (size_t i = 0; i < items.size(); ++i) {
+        const BatchItem& it = items[i];
+        BatchInst<R>& in = insts[i];
+        in.A = (R*)it.p->rows[it.p->cur];
+        in.B = (R*)it.p->rows[1 - it.p->cur];
+        in.N = it.p->N;
+        in.n = it.s.n;
+        in.H = it.s.H;
+        in.K = it.s.K;
+        in.bc = it.p->desc.bc;
+        in.Q = it.s.Q;
+        in.r = it.s.r;
+        in.n_phases = it.s.n_phases;
+        in.flag_off = (int)flags;
+        in.pad = 0;
+        in.c = coefs_of<R>(it.p);
+        flags += it.s.K;
+        max_phases = std::max(max_phases, it.s.n_phases);
+        max_n = std::max(max_n, it.s.n);
+    }
+    // (instance, phase) tasks, phase-major
+    std::vector<int2> tasks;
+    for (int64_t ph = 0; ph < max_phases; ++ph)
+        for (size_t i = 0; i < items.size(); ++i)
+            if (items[i].s.n_phases > ph) tasks.push_back(make_int2((int)i, (int)ph));
+    if (tasks.size() >= (size_t)1 << 30 || flags >= (int64_t)1 << 30)
+        return fail(SWP_EINVAL, "batch too large for one launch");
+    swp_status st;
+    if ((st = grow(&b->insts, &b->insts_cap, sizeof(BatchInst<R>) * insts.size())) != SWP_OK) return st;
+    if ((st = grow((void**)&b->tasks, &b->tasks_cap, sizeof(int2) * tasks.size())) != SWP_OK) return st;
+    if ((st = grow((void**)&b->ctr, &b->ctr_cap, sizeof(int) * (tasks.size() + 2))) != SWP_OK) return st;
+    if ((st = grow((void**)&b->flags, &b->flags_cap, sizeof(uint32_t) * (size_t)flags)) != SWP_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(b->insts, insts.data(), sizeof(BatchInst<R>) * insts.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->tasks, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctr, 0, sizeof(int) * (tasks.size() + 2), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch table upload");
+    // the staging vectors die at return: wait for the copies out of them
+    e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch table upload");
+    BatchWork w;
+    w.tasks = b->tasks;
+    w.cur_task = b->ctr;
+    w.status = b->ctr + 1;
+    w.task_ctr = b->ctr + 2;
+    w.ntasks = (int)tasks.size();
+    w.max_n = max_n;
+    w.flags = b->flags;
+    w.wait_limit_ns = b->wait_limit_ns;
+    const int bps = swept_batch_blocks_per_sm<R>(eq, max_n, threads);
+    if (bps <= 0) return fail(SWP_EINVAL, "batch kernel does not fit (max n=%d, threads=%d)", max_n, threads);
+    int64_t blocks = (int64_t)b->sms * bps;
+    int64_t items_total = 0;
+    for (auto& it : items) items_total += it.s.n_phases * it.s.K;
+    if (blocks > items_total) blocks = items_total;
+    e = launch_swept_batch<R>(eq, (const BatchInst<R>*)b->insts, w, threads, (int)blocks, b->stream);
+    b->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    for (auto& it : items) {
+        it.p->launches++;
+        if (it.s.top & 1) it.p->cur = 1 - it.p->cur;
+    }
+    return SWP_OK;
+}
+
+// Time `reps` advances of `steps` timesteps of `count` copies of a problem in
+// one batch at node width n; returns point-updates per second or < 0.
+double time_width(const swp_desc* desc, const void* u0, int count, int64_t steps, int n, int threads,
+                  cudaStream_t stream)
+{
+    std::vector<swp_problem*> probs;
+    double rate = -1.0;
+    swp_batch* b = nullptr;
+    std::vector<int64_t> st(count, steps);
+    std::vector<int32_t> nn(count, n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (swp_batch_create(stream, &b) != SWP_OK) return -1.0;
+    for (int i = 0; i < count; ++i) {
+        swp_problem* p = nullptr;
+        if (swp_create(desc, u0, 0, stream, &p) != SWP_OK) goto done;
+        probs.push_back(p);
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
+    if (swp_batch_advance(b, probs.data(), st.data(), count, nn.data(), threads) != SWP_OK) goto done;
+    if (swp_batch_synchronize(b) != SWP_OK) goto done;
+    cudaEventRecord(e0, stream);
+    if (swp_batch_advance(b, probs.data(), st.data(), count, nn.data(), threads) != SWP_OK) goto done;
+    cudaEventRecord(e1, stream);
+    if (swp_batch_synchronize(b) == SWP_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.f) rate = (double)count * desc->n_points * steps / (ms * 1e-3);
+    }
+done:
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (auto* p : probs) swp_destroy(p);
+    swp_batch_destroy(b);
+    return rate;
+}
+
+}  // namespace
+
+extern "C" {
+
+swp_status swp_batch_create(void* cuda_stream, swp_batch** out)
+{
+    if (!out) return fail(SWP_EINVAL, "out is NULL");
+    *out = nullptr;
+    swp_batch* b = new (std::nothrow) swp_batch();
+    if (!b) return fail(SWP_ENOMEM, "host allocation failed");
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return SWP_OK;
+}
+
+swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
+                             int32_t count, const int32_t* points_per_block, int32_t threads)
+{
+    if (!b || !problems || !n_steps) return fail(SWP_EINVAL, "batch, problems or n_steps is NULL");
+    if (count < 0) return fail(SWP_EINVAL, "count must be >= 0");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return fail(SWP_EINVAL, "current device differs from the batch's device");
+    std::vector<BatchItem> groups[3][2];
+    int max_threads = 1024;
+    for (int32_t i = 0; i < count; ++i) {
+        swp_problem* p = problems[i];
+        if (!p) return fail(SWP_EINVAL, "problem %d is NULL", i);
+        if (p->device != b->device) return fail(SWP_EINVAL, "problem %d is on another device", i);
+        if (p->stream != b->stream) return fail(SWP_EINVAL, "problem %d uses another stream than the batch", i);
+        if (n_steps[i] < 0 || n_steps[i] > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps[%d] out of range", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (problems[j] == p) return fail(SWP_EINVAL, "problem %d appears twice", i);
+        if (n_steps[i] == 0) continue;
+        int n = points_per_block ? points_per_block[i] : 0;
+        if (n == 0) n = width_for(p);
+        if (n == 0) return fail(SWP_EINVAL, "no valid node width for problem %d", i);
+        swp_status st = check_width(p, n);
+        if (st != SWP_OK) return st;
+        BatchItem it;
+        it.p = p;
+        it.s = plan_swept(p, n_steps[i], n);
+        groups[p->desc.eq][p->desc.dtype].push_back(it);
+        if (p->desc.eq == SWP_EULER) max_threads = 256;
+    }
+    if (threads == 0) threads = 256;
+    if (threads < 32 || threads > max_threads || threads % 32)
+        return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
+    for (int eq = 0; eq < 3; ++eq)
+        for (int dt = 0; dt < 2; ++dt) {
+            if (groups[eq][dt].empty()) continue;
+            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[eq][dt], eq, threads)
+                                          : batch_group<float>(b, groups[eq][dt], eq, threads);
+            if (st != SWP_OK) return st;
+        }
+    return SWP_OK;
+}
+
+swp_status swp_batch_synchronize(swp_batch* b)
+{
+    if (!b) return fail(SWP_EINVAL, "batch is NULL");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
+    if (b->ctr) {
+        int st = 0;
+        e = cudaMemcpy(&st, b->ctr + 1, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "batch status read");
+        if (st != 0) {
+            cudaMemset(b->ctr + 1, 0, sizeof(int));
+            return fail(SWP_ETIMEOUT, "a node's bounded wait gave up; the batch's states are invalid");
+        }
+    }
+    return SWP_OK;
+}
+
+swp_status swp_batch_destroy(swp_batch* b)
+{
+    if (!b) return SWP_OK;
+    if (b->insts) cudaFree(b->insts);
+    if (b->tasks) cudaFree(b->tasks);
+    if (b->ctr) cudaFree(b->ctr);
+    if (b->flags) cudaFree(b->flags);
+    delete b;
+    return SWP_OK;
+}
+
+int64_t swp_batch_kernel_launches(const swp_batch* b) { return b ? b->launches : -1; }
+
+swp_status swp_autotune_width(const swp_desc* desc, const void* u0_host, int32_t batch_count,
+                              int64_t steps, int32_t* best_n)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!u0_host || !best_n || batch_count <= 0 || steps <= 0)
+        return fail(SWP_EINVAL, "u0_host / best_n NULL or count, steps <= 0");
+    *best_n = 0;
+    swp_problem probe;   // for the width checks only
+    probe.desc = *desc;
+    probe.rad = radius_of(desc->eq);
+    probe.nv = nv_of(desc->eq);
+    probe.esize = esize_of(desc->dtype);
+    probe.N = desc->n_points;
+    if (cudaGetDevice(&probe.device) != cudaSuccess) return fail(SWP_EDEVICE, "no CUDA device");
+    const int cap = desc->eq == SWP_EULER ? 1024 : 4096;
+    double best = -1.0;
+    for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
+        if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
+        const int threads = desc->eq == SWP_EULER ? 128 : (n >= 512 ? 256 : 128);
+        const double rate = time_width(desc, u0_host, batch_count, steps, n, threads, nullptr);
+        if (rate > best) {
+            best = rate;
+            *best_n = n;
+        }
+    }
+    if (*best_n == 0) return fail(SWP_EINVAL, "no node width could be timed for n_points %lld", (long long)probe.N);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[std::make_tuple(desc->eq, desc->dtype, desc->n_points)] = *best_n;
+    return SWP_OK;
+}
+
+swp_status swp_tuned_width(const swp_desc* desc, int32_t* n)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!n) return fail(SWP_EINVAL, "n is NULL");
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(std::make_tuple(desc->eq, desc->dtype, desc->n_points));
+    *n = it == g_tuned.end() ? 0 : it->second;
+    return SWP_OK;
+}
 
 }  // extern "C"
 

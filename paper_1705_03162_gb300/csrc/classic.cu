@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
                 out[i] = heat_point(sm[s - 1], sm[s], sm[s + 1], c.fo);
             } else {
                 out[i] = ks_point(sm[s - 2], sm[s - 1], sm[s], sm[s + 1], sm[s + 2], base[i],
-                                  c.a1[stage], c.a4[stage], c.beta[stage]);
+                                  c.a1[stage], c.a4[stage], c.beta[stage], c.gam[stage]);
             }
         }
     }

@@ -60,4 +60,40 @@ cudaError_t launch_swept_persistent(int eq, int bc, R* A, R* B, const Persistent
 template <typename R>
 int swept_persistent_blocks_per_sm(int eq, int n, int threads);
 
+// ---------------------------------------------------------------------------
+// Batched swept advance: many independent problems of one equation and
+// precision in one persistent launch.  Work is a table of (instance, phase)
+// tasks in phase-major order; a block claims one node of the current task at
+// a time, so items are claimed in dependency order, and waits (bounded) for
+// the instance's two neighbouring nodes of the previous phase.
+// ---------------------------------------------------------------------------
+template <typename R> struct BatchInst {
+    R* A;                 // even-level row of the instance ([nv][N])
+    R* B;                 // odd-level row
+    int64_t N;
+    int n, H, K, bc;
+    int64_t Q, r, n_phases;
+    int flag_off;         // first flag of this instance
+    int pad;
+    Coefs<R> c;
+};
+
+struct BatchWork {
+    const int2* tasks;    // (instance, phase), phase-major
+    int* task_ctr;        // nodes claimed per task (zeroed per launch)
+    int* cur_task;        // first task with unclaimed nodes (zeroed per launch)
+    int ntasks;
+    int max_n;            // widest node of the launch (shared-memory size)
+    uint32_t* flags;      // completed phases per (instance, node), zeroed per launch
+    int* status;          // != 0: a wait gave up
+    uint64_t wait_limit_ns;
+};
+
+template <typename R>
+cudaError_t launch_swept_batch(int eq, const BatchInst<R>* insts, const BatchWork& w, int threads,
+                               int blocks, cudaStream_t s);
+
+template <typename R>
+int swept_batch_blocks_per_sm(int eq, int max_n, int threads);
+
 }  // namespace swp

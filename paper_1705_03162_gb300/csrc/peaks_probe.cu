@@ -81,6 +81,18 @@ __global__ void ffma_k(float* out, int iters, float a, float b) {
   if (s == 12345.678f) out[blockIdx.x*blockDim.x+threadIdx.x] = s;
 }
 __global__ void empty_k() {}
+// dependent FP64 chain: latency of one DFMA / DADD, one warp per block
+__global__ void dfma_lat_k(double* out, int iters, double a, double b) {
+  double x = threadIdx.x * 1e-9;
+  for (int i = 0; i < iters; ++i) x = fma(x, a, b);
+  if (x == 12345.678) out[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+// __syncthreads round trip with 8 warps and no other work
+__global__ void bar_k(double* out, int iters) {
+  double x = threadIdx.x;
+  for (int i = 0; i < iters; ++i) { __syncthreads(); x += 1.0; }
+  if (x == 12345.678) out[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
 // shared-memory bandwidth: each thread reads 8B words in a strided-free pattern
 __global__ void smem_k(double* out, int iters) {
   __shared__ double sm[4096];
@@ -143,6 +155,16 @@ int main() {
     cudaEventRecord(e0); smem_k<<<blocks,thr>>>(dout, iters); cudaEventRecord(e1); CK(cudaEventSynchronize(e1));
     cudaEventElapsedTime(&ms,e0,e1); double bytes=(double)blocks*thr*iters*2*8;
     printf("SMEM LDS.64 : %.3f ms %.2f TB/s  B/clk/SM(2070)=%.1f\n", ms, bytes/ms/1e9, bytes/(ms*1e-3)/sms/2.07e9); }
+  { int iters = 100000;
+    dfma_lat_k<<<sms, 32>>>(dout, 10, 1.0000001, 1e-7); CK(cudaDeviceSynchronize());
+    cudaEventRecord(e0); dfma_lat_k<<<sms, 32>>>(dout, iters, 1.0000001, 1e-7); cudaEventRecord(e1); CK(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms,e0,e1);
+    printf("DFMA dependent latency (1 warp/SM): %.2f ns = %.1f clk at 2070 MHz\n", ms*1e6/iters, ms*1e6/iters*2.07); }
+  { int iters = 100000;
+    bar_k<<<sms, 256>>>(dout, 10); CK(cudaDeviceSynchronize());
+    cudaEventRecord(e0); bar_k<<<sms, 256>>>(dout, iters); cudaEventRecord(e1); CK(cudaEventSynchronize(e1));
+    cudaEventElapsedTime(&ms,e0,e1);
+    printf("__syncthreads + DADD loop (8 warps): %.2f ns = %.1f clk per iteration\n", ms*1e6/iters, ms*1e6/iters*2.07); }
   // launch latency
   { int n=20000; for (int i=0;i<100;++i) empty_k<<<1,32>>>(); CK(cudaDeviceSynchronize());
     cudaEventRecord(e0); for (int i=0;i<n;++i) empty_k<<<1,32>>>(); cudaEventRecord(e1); CK(cudaEventSynchronize(e1));

@@ -37,8 +37,9 @@ template <> struct Fp<float> {
 // Per-problem constants, formed on the host in double and rounded once to R.
 template <typename R> struct Coefs {
     R fo;                 // heat: Fourier number alpha dt / dx^2
-    R a1[2], a4[2], beta[2];  // KS stage s (0 predictor h = dt/2, 1 final h = dt):
-                          // a1 = -h/(4dx), a4 = -h/dx^4, beta = -h/dx^2 - 4 a4
+    R a1[2], a4[2], beta[2], gam[2];  // KS stage s (0 predictor h = dt/2, 1 final h = dt):
+                          // a1 = -h/(4dx), a4 = -h/dx^4, beta = a2 - 4 a4,
+                          // gam = 6 a4 - 2 a2, a2 = -h/dx^2
     R kh[2];              // Euler stage s: -(h/dx)/2 (G below is twice the flux)
     R gm1, ggm1;          // gamma - 1, gamma (gamma - 1)
     R ghost_l[3], ghost_r[3];  // Dirichlet end states, conserved
@@ -59,22 +60,24 @@ __device__ __forceinline__ R heat_point(R tm, R t0, R tp, R fo)
 // ---------------------------------------------------------------------------
 // Kuramoto-Sivashinsky, one midpoint-RK2 stage (Appendix B, Eqs. KSDisc, RKm,
 // RKf): out = base + h f(v), base = u^m, h = dt/2 (predictor) or dt (final).
-// The fourth difference v++ - 4v+ + 6v - 4v- + v-- equals d2 - 4 lap with
-// lap = v+ + v- - 2v and d2 = v++ + v-- - 2v, so
-//   h f = a1 (v+^2 - v-^2) + a4 d2 + beta lap.
-// Nine FP operations per stage.
+// The Laplacian (1, -2, 1)/dx^2 and the fourth difference (1, -4, 6, -4, 1)/dx^4
+// combine into one five-point stencil with weights a4 (v++, v--),
+// beta = a2 - 4 a4 (v+, v-) and gam = 6 a4 - 2 a2 (v), so
+//   h f = a1 (v+^2 - v-^2) + a4 (v++ + v--) + beta (v+ + v-) + gam v,
+// with a1 = -h/(4dx), a2 = -h/dx^2, a4 = -h/dx^4.  Eight FP operations.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R ks_point(R vmm, R vm, R v0, R vp, R vpp, R base,
-                                      R a1, R a4, R beta)
+                                      R a1, R a4, R beta, R gam)
 {
     using F = Fp<R>;
+    // summed into base in the order gam, beta, a4, a1 terms: the first three
+    // need no product of neighbours, so the dependent chain is four deep
     R b = F::fma(vp, vp, -F::mul(vm, vm));
-    R lap = F::fma(R(-2), v0, F::add(vp, vm));
-    R d2 = F::fma(R(-2), v0, F::add(vpp, vmm));
-    R acc = F::fma(a1, b, base);
-    acc = F::fma(a4, d2, acc);
-    return F::fma(beta, lap, acc);
+    R acc = F::fma(gam, v0, base);
+    acc = F::fma(beta, F::add(vp, vm), acc);
+    acc = F::fma(a4, F::add(vpp, vmm), acc);
+    return F::fma(a1, b, acc);
 }
 
 // ---------------------------------------------------------------------------

@@ -148,12 +148,12 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
             }
         } else if constexpr (EQ == KS) {
             // KS problems are periodic: the window is already wrapped.
-            const R a1 = c.a1[stage], a4 = c.a4[stage], beta = c.beta[stage];
+            const R a1 = c.a1[stage], a4 = c.a4[stage], beta = c.beta[stage], gam = c.gam[stage];
             for (int t = threadIdx.x; t < cnt; t += T) {
                 const int q = lo + t;
                 const R base = stage == 0 ? src[q] : row0[q];
                 dst[q] = ks_point(src[q - 2], src[q - 1], src[q], src[q + 1], src[q + 2], base, a1,
-                                  a4, beta);
+                                  a4, beta, gam);
             }
         } else {
             const R kh = c.kh[stage];
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_ker
             const int kr = odd ? k : (k + 1) % K;
             const uint32_t need = plan.flag_base + (uint32_t)p + plan.wait_offset;
             const uint64_t t_start = global_ns();
-            uint32_t polls = 0;
+            uint32_t polls = 0, backoff = 32;
             while ((int32_t)(ld_acquire(flags + kl) - need) < 0 ||
                    (int32_t)(ld_acquire(flags + kr) - need) < 0) {
                 if (ld_volatile(status) != 0 || ++polls > kMaxPolls ||
@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_ker
                     abort_s = 1;
                     break;
                 }
-                __nanosleep(polls < 64 ? 32 : 256);
+                __nanosleep(backoff);
+                if (backoff < 1024) backoff *= 2;
             }
         }
         __syncthreads();
@@ -350,6 +351,83 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_ker
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) st_release(flags + k, plan.flag_base + (uint32_t)p + 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent form (many independent problems of one equation).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_relaxed(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename R, int EQ>
+__global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
+                                                                              BatchWork w)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int task_s, node_s, abort_s;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            // claim the next node of the first task with unclaimed nodes
+            int t = ld_relaxed(w.cur_task), k = -1;
+            while (t < w.ntasks) {
+                const int K = insts[w.tasks[t].x].K;
+                k = atomicAdd(w.task_ctr + t, 1);
+                if (k < K) break;
+                atomicCAS(w.cur_task, t, t + 1);
+                t = ld_relaxed(w.cur_task);
+            }
+            task_s = t;
+            node_s = k;
+            abort_s = 0;
+        }
+        __syncthreads();
+        const int t = task_s;
+        if (t >= w.ntasks) break;
+        const int2 tk = w.tasks[t];
+        const BatchInst<R>& in = insts[tk.x];
+        const int64_t p = tk.y;
+        const int k = node_s, K = in.K, H = in.H, n = in.n;
+        const int odd = (int)(p & 1);
+        const int j_lo = p == 0 ? H + 1 : 1;
+        const int j_hi = p < in.Q ? 2 * H - 1 : (p == in.Q ? H + (int)in.r : (int)in.r);
+        if (p > 0 && threadIdx.x == 0) {
+            const int kl = odd ? (k + K - 1) % K : k;
+            const int kr = odd ? k : (k + 1) % K;
+            const uint32_t need = (uint32_t)p;
+            const uint32_t* f = w.flags + in.flag_off;
+            const uint64_t t_start = global_ns();
+            uint32_t polls = 0, backoff = 32;
+            while (ld_acquire(f + kl) < need || ld_acquire(f + kr) < need) {
+                if (ld_volatile(w.status) != 0 || ++polls > kMaxPolls ||
+                    global_ns() - t_start > w.wait_limit_ns) {
+                    atomicExch(w.status, 1);
+                    abort_s = 1;
+                    break;
+                }
+                __nanosleep(backoff);
+                if (backoff < 1024) backoff *= 2;
+            }
+        }
+        __syncthreads();
+        if (abort_s) break;
+        R *row0, *row1, *P, *G;
+        smem_rows<R, EQ>(smem_raw, n, row0, row1, P, G);
+        const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
+        const int64_t g0 = xc - n / 2 - RAD;
+        window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
+        __syncthreads();
+        tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N,
+                           node_near_wall(in.bc, k, K), in.bc, in.c);
+        window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(w.flags + in.flag_off + k, (uint32_t)p + 1);
     }
 }
 
@@ -394,6 +472,29 @@ int persistent_bps_eq(int n, int threads)
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_persistent_kernel<R, EQ>, threads,
                                                       smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <typename R, int EQ>
+cudaError_t batch_launch_eq(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
+                            cudaStream_t s)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(w.max_n);
+    cudaError_t e = set_smem<R, EQ>((const void*)swept_batch_kernel<R, EQ>, smem);
+    if (e != cudaSuccess) return e;
+    swept_batch_kernel<R, EQ><<<blocks, threads, smem, s>>>(insts, w);
+    return cudaGetLastError();
+}
+
+template <typename R, int EQ>
+int batch_bps_eq(int max_n, int threads)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(max_n);
+    if (set_smem<R, EQ>((const void*)swept_batch_kernel<R, EQ>, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, EQ>, threads, smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
@@ -460,6 +561,33 @@ template cudaError_t launch_swept_persistent<float>(int, int, float*, float*,
                                                     const PersistentPlan&, const Coefs<float>&,
                                                     uint32_t*, unsigned int*, int*, int, int,
                                                     cudaStream_t);
+template <typename R>
+cudaError_t launch_swept_batch(int eq, const BatchInst<R>* insts, const BatchWork& w, int threads,
+                               int blocks, cudaStream_t s)
+{
+    switch (eq) {
+    case HEAT: return batch_launch_eq<R, HEAT>(insts, w, threads, blocks, s);
+    case KS: return batch_launch_eq<R, KS>(insts, w, threads, blocks, s);
+    default: return batch_launch_eq<R, EULER>(insts, w, threads, blocks, s);
+    }
+}
+
+template <typename R>
+int swept_batch_blocks_per_sm(int eq, int max_n, int threads)
+{
+    switch (eq) {
+    case HEAT: return batch_bps_eq<R, HEAT>(max_n, threads);
+    case KS: return batch_bps_eq<R, KS>(max_n, threads);
+    default: return batch_bps_eq<R, EULER>(max_n, threads);
+    }
+}
+
+template cudaError_t launch_swept_batch<double>(int, const BatchInst<double>*, const BatchWork&, int,
+                                                int, cudaStream_t);
+template cudaError_t launch_swept_batch<float>(int, const BatchInst<float>*, const BatchWork&, int,
+                                               int, cudaStream_t);
+template int swept_batch_blocks_per_sm<double>(int, int, int);
+template int swept_batch_blocks_per_sm<float>(int, int, int);
 template int swept_persistent_blocks_per_sm<double>(int, int, int);
 template int swept_persistent_blocks_per_sm<float>(int, int, int);
 

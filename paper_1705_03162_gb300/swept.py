@@ -38,6 +38,8 @@ ABI_SYMBOLS = (
     "swp_destroy", "swp_shape", "swp_kernel_launches", "swp_required_bytes",
     "swp_set_memory_budget", "swp_memory_in_use", "swp_debug_withhold_flags",
     "swp_status_str", "swp_last_error", "swp_swept_noalloc",
+    "swp_batch_create", "swp_batch_advance", "swp_batch_synchronize", "swp_batch_destroy",
+    "swp_batch_kernel_launches", "swp_autotune_width", "swp_tuned_width",
 )
 
 
@@ -99,6 +101,14 @@ def load_library(path: str = LIB_PATH):
             "swp_memory_in_use": ([], sz),
             "swp_debug_withhold_flags": ([P, ctypes.c_int, i64], ctypes.c_int),
             "swp_swept_noalloc": ([ctypes.POINTER(Desc), vp, i64, i32, i32, vp], ctypes.c_int),
+            "swp_batch_create": ([vp, ctypes.POINTER(P)], ctypes.c_int),
+            "swp_batch_advance": ([P, ctypes.POINTER(P), ctypes.POINTER(i64), i32,
+                                   ctypes.POINTER(i32), i32], ctypes.c_int),
+            "swp_batch_synchronize": ([P], ctypes.c_int),
+            "swp_batch_destroy": ([P], ctypes.c_int),
+            "swp_batch_kernel_launches": ([P], i64),
+            "swp_autotune_width": ([ctypes.POINTER(Desc), vp, i32, i64, ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_tuned_width": ([ctypes.POINTER(Desc), ctypes.POINTER(i32)], ctypes.c_int),
             "swp_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "swp_last_error": ([], ctypes.c_char_p),
         }
@@ -258,3 +268,63 @@ def swept_noalloc(spec: ProblemSpec, state, steps: int, n: int = 0, threads: int
     _check(lib.swp_swept_noalloc(ctypes.byref(desc), ctypes.c_void_p(ptr), int(steps), int(n),
                                  int(threads), ctypes.c_void_p(handle)), "swept_noalloc")
     return state
+
+
+class Batch:
+    """Batched swept advance: many problems (created with this batch's stream)
+    advanced together in one persistent launch per (equation, dtype) group."""
+
+    def __init__(self, stream=None):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p(0)
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
+        _check(self._lib.swp_batch_create(ctypes.c_void_p(handle), ctypes.byref(self._h)), "batch_create")
+
+    def advance(self, problems, steps, n=None, threads: int = 0):
+        count = len(problems)
+        hs = (ctypes.c_void_p * count)(*[p._h.value for p in problems])
+        st = (ctypes.c_int64 * count)(*[int(x) for x in steps])
+        nn = None if n is None else (ctypes.c_int32 * count)(*[int(x) for x in n])
+        _check(self._lib.swp_batch_advance(self._h, hs, st, count, nn, int(threads)), "batch_advance")
+
+    def synchronize(self):
+        _check(self._lib.swp_batch_synchronize(self._h), "batch_synchronize")
+
+    def kernel_launches(self) -> int:
+        return int(self._lib.swp_batch_kernel_launches(self._h))
+
+    def close(self):
+        if self._h and self._h.value:
+            _check(self._lib.swp_batch_destroy(self._h), "batch_destroy")
+            self._h = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_width(spec: ProblemSpec, u0: np.ndarray, count: int = 16, steps: int = 200,
+                   dtype: str = "f64") -> int:
+    """Time ``count`` copies of the problem in one batch for each node width and
+    keep the fastest for later batches of this (equation, dtype, N)."""
+    lib = load_library()
+    u0 = np.ascontiguousarray(u0)
+    out = ctypes.c_int32(0)
+    _check(lib.swp_autotune_width(ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data, int(count),
+                                  int(steps), ctypes.byref(out)), "autotune_width")
+    return out.value
+
+
+def tuned_width(spec: ProblemSpec, dtype: str = "f64") -> int:
+    out = ctypes.c_int32(0)
+    _check(load_library().swp_tuned_width(ctypes.byref(make_desc(spec, dtype)), ctypes.byref(out)),
+           "tuned_width")
+    return out.value
