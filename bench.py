@@ -52,7 +52,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC = {
     # profiles/swept_phase_kernel_ks_n512.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
-    "swept_phase_kernel<double,KS> n=512": {"src": "cc59ea96f376ed8e", "bytes_per_launch": 16784384},
+    "swept_phase_kernel<double,KS> n=512": {"src": "f50502abd4fe5fde", "bytes_per_launch": 16784128},
 }
 
 
@@ -205,6 +205,157 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+
+# ---------------------------------------------------------------------------
+# batched and served workloads, FP32 error (single GPU)
+# ---------------------------------------------------------------------------
+def _spec_ic(eq: str, N: int, dtype=np.float64):
+    spec = I.heat_spec(N) if eq == "heat" else (I.ks_spec(N) if eq == "ks" else I.sod_spec(N))
+    return spec, I.initial_state(spec, dtype)
+
+
+def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
+    """4096 independent heat + KS instances, N log-uniform 2^10..2^16, steps
+    U(10^3, 10^4), one persistent launch per precision, autotuned node widths;
+    against advancing a sample of the same instances one by one."""
+    import math
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    rng = np.random.default_rng(seed)
+    cases = []
+    for i in range(count):
+        N = max(1024, int(round(2 ** rng.uniform(10, 16) / 128)) * 128)
+        cases.append(("heat" if i % 2 == 0 else "ks", N, int(rng.integers(1000, 10001))))
+    out = {"instances": count, "workload": "heat+KS, N log-uniform 2^10..2^16, steps U(1e3,1e4)"}
+    for dtype in ("f64", "f32"):
+        npdt = np.float64 if dtype == "f64" else np.float32
+        t0 = time.perf_counter()
+        tuned = {}
+        for eq in ("heat", "ks"):
+            for e in range(10, 17):
+                spec, u0 = _spec_ic(eq, 2 ** e, npdt)
+                tuned[(eq, e)] = S.autotune_width(spec, u0, count=32, steps=256, dtype=dtype)
+        tune_s = time.perf_counter() - t0
+        stream = torch.cuda.Stream()
+        probs, widths = [], []
+        for eq, N, steps in cases:
+            spec, u0 = _spec_ic(eq, N, npdt)
+            probs.append(S.Problem(spec, u0, dtype, stream=stream))
+            n = tuned[(eq, min(max(int(round(math.log2(N))), 10), 16))]
+            while N % n:
+                n //= 2
+            widths.append(n)
+        steps = [c[2] for c in cases]
+        upd = float(sum(c[1] * c[2] for c in cases))
+        with S.Batch(stream) as bt:
+            bt.advance(probs, [min(s, 64) for s in steps], widths)   # warm-up
+            bt.synchronize()
+            l0 = bt.kernel_launches()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            bt.advance(probs, steps, widths)
+            ev1.record(stream)
+            bt.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            launches = bt.kernel_launches() - l0
+        sample = range(32)
+        su = float(sum(cases[i][1] * cases[i][2] for i in sample))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in sample:
+            probs[i].advance(steps[i], "swept", widths[i])
+        torch.cuda.synchronize()
+        per_inst = su / (time.perf_counter() - t0) / 1e9
+        for p in probs:
+            p.close()
+        out[dtype] = {"value": upd / ms / 1e6, "unit": UNIT, "ms": ms, "kernel_launches": launches,
+                      "per_instance_swept_value": per_inst, "autotune_s": tune_s,
+                      "tuned_widths": {f"{k[0]}2^{k[1]}": v for k, v in tuned.items()}}
+    return out
+
+
+def _trace(count: int, lam: float, seed: int):
+    rng = np.random.default_rng(seed)
+    t, reqs = 0.0, []
+    for i in range(count):
+        t += rng.exponential(1.0 / lam)
+        eq = ("heat", "ks", "euler")[int(rng.integers(0, 3))]
+        N = max(1024, int(round(2 ** rng.uniform(10, 20) / 1024)) * 1024)
+        reqs.append((t, eq, N, int(rng.integers(1000, 10001))))
+    return reqs
+
+
+def _percentiles(lat):
+    lat = np.sort(np.asarray(lat))
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+
+
+def run_served(count: int, lam: float, seed: int, budget: int, baseline: bool = True) -> dict:
+    """Poisson arrivals of mixed heat / KS / Euler solves (FP64) served with
+    continuous batching, and the same trace solved one request at a time."""
+    import threading
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    reqs = _trace(count, lam, seed)
+    inputs = [_spec_ic(eq, N) for _, eq, N, _ in reqs]
+    upd = float(sum(N * st for _, _, N, st in reqs))
+    res = {"requests": count, "lambda_per_s": lam, "hbm_budget_bytes": budget,
+           "mix": "heat/KS/Euler uniform, N log-uniform 2^10..2^20, steps U(1e3,1e4), FP64"}
+    with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=5.0) as srv:
+        ids = [None] * count
+        t_start = time.perf_counter()
+
+        def feed():
+            for i, (t_arr, eq, N, st) in enumerate(reqs):
+                d = t_start + t_arr - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                spec, u0 = inputs[i]
+                ids[i] = srv.submit(spec, u0, st)
+
+        th = threading.Thread(target=feed)
+        th.start()
+        th.join()
+        lat = [srv.wait(i)[1] for i in ids]
+        span = time.perf_counter() - t_start
+        stats = srv.stats()
+    res["served"] = dict(_percentiles(lat), throughput=upd / span / 1e9, unit=UNIT,
+                         rounds=stats["rounds"], kernel_launches=stats["kernel_launches"])
+    if baseline:
+        lat_b = []
+        t_start = time.perf_counter()
+        for i, (t_arr, eq, N, st) in enumerate(reqs):
+            d = t_start + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            spec, u0 = inputs[i]
+            with S.Problem(spec, u0) as p:
+                p.advance(st, "swept")
+                p.read()
+            lat_b.append(time.perf_counter() - (t_start + t_arr))
+        span_b = time.perf_counter() - t_start
+        res["per_instance"] = dict(_percentiles(lat_b), throughput=upd / span_b / 1e9, unit=UNIT)
+    return res
+
+
+def fp32_error() -> dict:
+    """FP32 heat / KS against the FP64 oracle (reported, not gated)."""
+    import oracle as O
+    from paper_1705_03162_gb300 import swept as S
+    out = {}
+    for name, spec, steps in (("heat N=1024 r=0.25 4096 steps", I.heat_spec(1024), 4096),
+                              ("KS N=2^11 10^4 steps", I.ks_spec(2048), 10_000)):
+        u64 = I.initial_state(spec)
+        ref = u64.copy()
+        eq = O.HEAT if spec.eq == "heat" else O.KS
+        O.classic(O.OracleProblem(eq, O.PERIODIC, spec.n_points, spec.dx, spec.dt, spec.alpha), ref, steps)
+        with S.Problem(spec, u64.astype(np.float32), "f32") as p:
+            p.advance(steps, "swept")
+            got = p.read().astype(np.float64)
+        out[name] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    return out
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -330,6 +481,13 @@ def run_gpu(args, wl):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(wl)
+    if world == 1 and not args.no_extras:
+        line["served"] = {
+            "lambda_2000": run_served(48, 2000.0, 20170509, 1 << 30),
+            "below_saturation": run_served(24, 2.5, 20170510, 1 << 30, baseline=True),
+        }
+        line["batched"] = run_batched()
+        line["fp32_rel_error_vs_fp64_oracle"] = fp32_error()
     print(json.dumps(line), flush=True)
     dist.close()
 
@@ -345,6 +503,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--timesteps", type=int, default=DEFAULT_WORKLOAD["steps"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the served, batched and FP32-error measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

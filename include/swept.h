@@ -88,14 +88,19 @@ typedef enum {
     SWP_LAUNCH_AUTO = 0,        /* library choice */
     SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
                                    nodes synchronise at kernel boundaries */
-    SWP_LAUNCH_PERSISTENT = 2   /* one kernel for the whole advance; each node
+    SWP_LAUNCH_PERSISTENT = 2,  /* one kernel for the whole advance; each node
                                    waits (bounded) on its two neighbours' flags */
+    SWP_LAUNCH_GRAPH = 3        /* the per-phase (swept) or per-sub-step (classic)
+                                   launches as a CUDA graph, captured on first use
+                                   for (scheme, n_steps, width, threads) and
+                                   replayed afterwards */
 } swp_launch;
 
 typedef struct {
     int32_t scheme;            /* swp_scheme */
     int32_t points_per_block;  /* swept node width n (0 = auto); classic: unused */
-    int32_t launch;            /* swp_launch */
+    int32_t launch;            /* swp_launch (classic: AUTO / PER_PHASE = stream
+                                  launches, GRAPH = graph replay) */
     int32_t threads;           /* threads per block (0 = auto; multiple of 32) */
 } swp_advance_opts;
 
@@ -154,7 +159,8 @@ size_t swp_memory_in_use(void);
 /* ---- Batched swept advance (many independent problems, one launch) ----
  * Advancing many small problems one by one leaves most of the GPU idle and
  * pays a launch per phase each.  A batch advances every problem given to it
- * in one persistent launch per (equation, dtype) group: work is a table of
+ * in one persistent launch per precision (heat and KS together, Euler in a
+ * launch of its own): work is a table of
  * (problem, phase) tasks in phase-major order; each block claims one node of
  * the current task at a time and waits, bounded, for the problem's two
  * neighbouring nodes of the previous phase (the paper's kernel-boundary
@@ -188,6 +194,48 @@ swp_status swp_autotune_width(const swp_desc* desc, const void* u0_host, int32_t
                               int64_t steps, int32_t* best_n);
 /* The tuned width for desc's (equation, dtype, n_points), or 0 if none. */
 swp_status swp_tuned_width(const swp_desc* desc, int32_t* n);
+
+/* ---- Serving with continuous batching ----
+ * A server owns a scheduler thread that admits solve requests as they arrive
+ * (in order, while its device-memory budget and slot count allow), keeps their
+ * states resident on the device, and advances all admitted requests together
+ * in rounds of batched launches; requests arriving meanwhile join the next
+ * round.  Each result is bit-identical to solving the request alone.  The
+ * paper has no serving layer. */
+typedef struct swp_server swp_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device bytes the server may hold (0 = no limit);
+                                 a request needing more than all of it fails
+                                 with SWP_EBUDGET */
+    int32_t max_active;       /* requests admitted at once (> 0) */
+    int32_t threads;          /* block size of the batched launches (0 = 256) */
+    double round_target_ms;   /* GPU time aimed at per round (> 0) */
+} swp_server_config;
+
+typedef struct {
+    int64_t completed, rounds, kernel_launches, pending, active;
+    size_t device_bytes_in_use;
+    double point_updates;     /* grid points x timesteps completed */
+    double busy_span_s;       /* first submission to last completion */
+} swp_server_statistics;
+
+/* Start a server whose GPU work runs on cuda_stream of the current device. */
+swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, swp_server** out);
+/* Queue a solve of n_steps (>= 1) timesteps from u0_host (copied before the
+ * call returns); request_id receives its id.  Thread-safe. */
+swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0_host, int64_t n_steps,
+                             int64_t* request_id);
+/* done = 1 once the request has finished (successfully or not). */
+swp_status swp_server_poll(swp_server* s, int64_t request_id, int32_t* done);
+/* Block until the request finishes; copy its final state to dst_host (NULL:
+ * discard) and its latency (submission to completion, seconds) to latency_s.
+ * Returns the request's status; the id is released. */
+swp_status swp_server_wait(swp_server* s, int64_t request_id, void* dst_host, size_t dst_bytes,
+                           double* latency_s);
+swp_status swp_server_stats(swp_server* s, swp_server_statistics* out);
+/* Finish admitted work, fail unadmitted requests, stop the thread, free all. */
+swp_status swp_server_destroy(swp_server* s);
 
 /* Fault-injection hook for tests of the persistent launch's bounded waits.
  * withhold != 0 makes every neighbour wait of later SWP_LAUNCH_PERSISTENT

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswept.so")
-SOURCES = ["api.cu", "classic.cu", "swept.cu"]
+SOURCES = ["api.cu", "classic.cu", "swept.cu", "server.cu"]
 HEADERS = ["scheme.cuh", "launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -43,6 +43,15 @@ struct swp_problem {
     uint64_t wait_limit_ns = 2000000000ull;   // bound of one neighbour wait
     unsigned int* counter = nullptr;
     int* status = nullptr;
+    // CUDA graphs of launch sequences (SWP_LAUNCH_GRAPH), replayed on `stream`
+    struct Graph {
+        int scheme, n, threads, cur_before, cur_after;
+        int64_t steps;
+        int64_t kernels;
+        cudaGraphExec_t exec;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -324,10 +333,81 @@ swp_status check_device_status(swp_problem* p)
     return SWP_OK;
 }
 
+// Run the launch sequence of an advance as a CUDA graph: captured once per
+// (scheme, steps, node width, threads, starting row) on a private stream,
+// then replayed on the problem's stream.
+template <typename R>
+swp_status run_graph(swp_problem* p, int64_t steps, int scheme, int n, int threads,
+                     const SweptPlan* s)
+{
+    for (auto& g : p->graphs)
+        if (g.scheme == scheme && g.steps == steps && g.n == n && g.threads == threads &&
+            g.cur_before == p->cur) {
+            cudaError_t e = cudaGraphLaunch(g.exec, p->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+            p->cur = g.cur_after;
+            p->launches += g.kernels;
+            return SWP_OK;
+        }
+    cudaError_t e;
+    if (!p->capture_stream) {
+        e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+    }
+    swp_problem::Graph g;
+    g.scheme = scheme;
+    g.steps = steps;
+    g.n = n;
+    g.threads = threads;
+    g.cur_before = p->cur;
+    const cudaStream_t user = p->stream;
+    const int64_t launches0 = p->launches;
+    e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+    p->stream = p->capture_stream;
+    swp_status st = scheme == SWP_CLASSIC ? run_classic<R>(p, steps, threads) : run_swept_phases<R>(p, *s, threads);
+    p->stream = user;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->capture_stream, &graph);
+    if (st != SWP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        p->cur = g.cur_before;
+        p->launches = launches0;
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    if (scheme == SWP_SWEPT && (s->top & 1)) p->cur = 1 - p->cur;
+    g.cur_after = p->cur;
+    g.kernels = p->launches - launches0;
+    p->launches = launches0;
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        p->cur = g.cur_before;
+        return cuda_fail(e, "graph instantiate");
+    }
+    if (p->graphs.size() >= 8) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back(g);
+    e = cudaGraphLaunch(g.exec, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    p->launches += g.kernels;
+    return SWP_OK;
+}
+
 template <typename R>
 swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& o)
 {
-    if (o.scheme == SWP_CLASSIC) return run_classic<R>(p, steps, o.threads);
+    if (o.scheme == SWP_CLASSIC) {
+        if (o.launch == SWP_LAUNCH_GRAPH) {
+            const int thr = o.threads <= 0 ? 256 : o.threads;
+            if (thr > 256 || thr % 32) return fail(SWP_EINVAL, "classic threads must be a multiple of 32 <= 256");
+            return run_graph<R>(p, steps, SWP_CLASSIC, 0, thr, nullptr);
+        }
+        return run_classic<R>(p, steps, o.threads);
+    }
     int n = o.points_per_block;
     if (n == 0) {
         n = default_width(p);
@@ -343,6 +423,7 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     const SweptPlan s = plan_swept(p, steps, n);
     if (s.T == 0) return SWP_OK;
     int launch = o.launch == SWP_LAUNCH_AUTO ? SWP_LAUNCH_PER_PHASE : o.launch;
+    if (launch == SWP_LAUNCH_GRAPH) return run_graph<R>(p, steps, SWP_SWEPT, n, threads, &s);
     if (launch == SWP_LAUNCH_PERSISTENT) st = run_swept_persistent<R>(p, s, threads);
     else if (launch == SWP_LAUNCH_PER_PHASE) st = run_swept_phases<R>(p, s, threads);
     else return fail(SWP_EINVAL, "unknown launch mode %d", o.launch);
@@ -507,6 +588,8 @@ swp_status swp_destroy(swp_problem* p)
     if (p->rows[0]) e = cudaFree(p->rows[0]);
     if (p->flags) cudaFree(p->flags);
     if (p->counter) cudaFree(p->counter);
+    for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     g_in_use -= p->bytes;
     delete p;
     if (e != cudaSuccess) return cuda_fail(e, "free");
@@ -604,11 +687,11 @@ struct BatchItem {
 };
 
 template <typename R>
-swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int eq, int threads)
+swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads)
 {
     std::vector<BatchInst<R>> insts(items.size());
     int64_t flags = 0, max_phases = 0;
-    int max_n = 0;
+    size_t smem = 0;
     for (size_t i = 0; i < items.size(); ++i) {
         const BatchItem& it = items[i];
         BatchInst<R>& in = insts[i];
@@ -623,11 +706,11 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int eq
         in.r = it.s.r;
         in.n_phases = it.s.n_phases;
         in.flag_off = (int)flags;
-        in.pad = 0;
+        in.eq = it.p->desc.eq;
         in.c = coefs_of<R>(it.p);
         flags += it.s.K;
         max_phases = std::max(max_phases, it.s.n_phases);
-        max_n = std::max(max_n, it.s.n);
+        smem = std::max(smem, swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
     }
     // (instance, phase) tasks, phase-major
     std::vector<int2> tasks;
@@ -657,16 +740,16 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int eq
     w.status = b->ctr + 1;
     w.task_ctr = b->ctr + 2;
     w.ntasks = (int)tasks.size();
-    w.max_n = max_n;
+    w.smem_bytes = smem;
     w.flags = b->flags;
     w.wait_limit_ns = b->wait_limit_ns;
-    const int bps = swept_batch_blocks_per_sm<R>(eq, max_n, threads);
-    if (bps <= 0) return fail(SWP_EINVAL, "batch kernel does not fit (max n=%d, threads=%d)", max_n, threads);
+    const int bps = swept_batch_blocks_per_sm<R>(mode, smem, threads);
+    if (bps <= 0) return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
     int64_t blocks = (int64_t)b->sms * bps;
     int64_t items_total = 0;
     for (auto& it : items) items_total += it.s.n_phases * it.s.K;
     if (blocks > items_total) blocks = items_total;
-    e = launch_swept_batch<R>(eq, (const BatchInst<R>*)b->insts, w, threads, (int)blocks, b->stream);
+    e = launch_swept_batch<R>(mode, (const BatchInst<R>*)b->insts, w, threads, (int)blocks, b->stream);
     b->launches++;
     if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     for (auto& it : items) {
@@ -741,7 +824,7 @@ swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
         return fail(SWP_EINVAL, "current device differs from the batch's device");
-    std::vector<BatchItem> groups[3][2];
+    std::vector<BatchItem> groups[2][2];   // [heat+KS | Euler][dtype]
     int max_threads = 1024;
     for (int32_t i = 0; i < count; ++i) {
         swp_problem* p = problems[i];
@@ -760,17 +843,19 @@ swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const i
         BatchItem it;
         it.p = p;
         it.s = plan_swept(p, n_steps[i], n);
-        groups[p->desc.eq][p->desc.dtype].push_back(it);
+        groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
         if (p->desc.eq == SWP_EULER) max_threads = 256;
     }
     if (threads == 0) threads = 256;
     if (threads < 32 || threads > max_threads || threads % 32)
         return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
-    for (int eq = 0; eq < 3; ++eq)
+    for (int g = 0; g < 2; ++g)
         for (int dt = 0; dt < 2; ++dt) {
-            if (groups[eq][dt].empty()) continue;
-            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[eq][dt], eq, threads)
-                                          : batch_group<float>(b, groups[eq][dt], eq, threads);
+            if (groups[g][dt].empty()) continue;
+            const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
+            const int thr = (g == 1 && threads > 256) ? 256 : threads;
+            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr)
+                                          : batch_group<float>(b, groups[g][dt], mode, thr);
             if (st != SWP_OK) return st;
         }
     return SWP_OK;

@@ -61,8 +61,8 @@ template <typename R>
 int swept_persistent_blocks_per_sm(int eq, int n, int threads);
 
 // ---------------------------------------------------------------------------
-// Batched swept advance: many independent problems of one equation and
-// precision in one persistent launch.  Work is a table of (instance, phase)
+// Batched swept advance: many independent problems of one precision in one
+// persistent launch (heat and KS together; Euler in its own launch).  Work is a table of (instance, phase)
 // tasks in phase-major order; a block claims one node of the current task at
 // a time, so items are claimed in dependency order, and waits (bounded) for
 // the instance's two neighbouring nodes of the previous phase.
@@ -74,7 +74,7 @@ template <typename R> struct BatchInst {
     int n, H, K, bc;
     int64_t Q, r, n_phases;
     int flag_off;         // first flag of this instance
-    int pad;
+    int eq;               // HEAT or KS (heat / KS launch), EULER
     Coefs<R> c;
 };
 
@@ -83,17 +83,18 @@ struct BatchWork {
     int* task_ctr;        // nodes claimed per task (zeroed per launch)
     int* cur_task;        // first task with unclaimed nodes (zeroed per launch)
     int ntasks;
-    int max_n;            // widest node of the launch (shared-memory size)
+    size_t smem_bytes;    // dynamic shared memory of the launch (widest node)
     uint32_t* flags;      // completed phases per (instance, node), zeroed per launch
     int* status;          // != 0: a wait gave up
     uint64_t wait_limit_ns;
 };
 
+// mode: HEAT for a heat / KS launch, EULER for an Euler launch
 template <typename R>
-cudaError_t launch_swept_batch(int eq, const BatchInst<R>* insts, const BatchWork& w, int threads,
+cudaError_t launch_swept_batch(int mode, const BatchInst<R>* insts, const BatchWork& w, int threads,
                                int blocks, cudaStream_t s);
 
 template <typename R>
-int swept_batch_blocks_per_sm(int eq, int max_n, int threads);
+int swept_batch_blocks_per_sm(int mode, size_t smem_bytes, int threads);
 
 }  // namespace swp

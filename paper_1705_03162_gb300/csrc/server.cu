@@ -1,0 +1,330 @@
+// Serving loop with continuous batching, on top of the public C ABI.
+//
+// Solve requests (problem description, initial state, step count) arrive at
+// any time from any thread.  A scheduler thread owns the GPU work:
+//  - admission: pending requests enter in arrival order while the server's
+//    device-memory budget and its slot count allow (a request larger than the
+//    whole budget fails with SWP_EBUDGET); an admitted request's state stays
+//    resident on the device until it finishes;
+//  - rounds: every active request advances by a chunk of timesteps sized to
+//    an equal share of a target round time (estimated FP64 work per
+//    point-update of each equation), all in one batched launch per group
+//    (swp_batch_advance); requests that arrive meanwhile join the next round,
+//    so new and in-flight work overlap on the device;
+//  - retirement: finished requests are copied back to host memory, their
+//    device memory is freed, and waiters are woken.
+// A swept advance always ends on a complete state and chunked advances are
+// bit-identical to one long advance, so a request's result does not depend on
+// what else was in the mix.  The paper has no serving layer; this is the
+// GB300 build's.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/swept.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t id = 0;
+    swp_desc desc{};
+    std::vector<unsigned char> u0;       // host copy of the initial state
+    std::vector<unsigned char> result;   // host copy of the final state
+    int64_t steps_total = 0, steps_done = 0;
+    int state = 0;                       // 0 pending, 1 active, 2 done
+    swp_status status = SWP_OK;
+    swp_problem* prob = nullptr;
+    size_t bytes = 0;                    // device bytes while active
+    Clock::time_point t_submit, t_admit, t_done;
+};
+
+size_t state_bytes(const swp_desc& d)
+{
+    return (size_t)(d.eq == SWP_EULER ? 3 : 1) * (size_t)d.n_points * (d.dtype == SWP_F32 ? 4 : 8);
+}
+
+// Estimated FP64-pipe operations per point-update (FP32: an eighth).
+double cost_per_update(const swp_desc& d)
+{
+    const double c = d.eq == SWP_HEAT ? 3.0 : (d.eq == SWP_KS ? 16.0 : 450.0);
+    return d.dtype == SWP_F32 ? c / 8.0 : c;
+}
+
+}  // namespace
+
+struct swp_server {
+    swp_server_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    swp_batch* batch = nullptr;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::thread worker;
+    int64_t next_id = 1;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::vector<std::shared_ptr<Request>> active;
+    std::map<int64_t, std::shared_ptr<Request>> all;
+    size_t in_use = 0;
+    // statistics
+    int64_t rounds = 0, completed = 0, launches = 0;
+    double point_updates = 0.0;
+    Clock::time_point t_first_submit, t_last_done;
+    bool any_submit = false;
+
+    void run();
+    void admit();
+    swp_status round();
+    void retire_finished();
+};
+
+void swp_server::admit()
+{
+    // called with mu held
+    while (!pending.empty() && (int)active.size() < cfg.max_active) {
+        auto r = pending.front();
+        const size_t need = 2 * state_bytes(r->desc);
+        if (cfg.hbm_budget_bytes && need > cfg.hbm_budget_bytes) {
+            pending.pop_front();
+            r->status = SWP_EBUDGET;
+            r->state = 2;
+            r->t_done = Clock::now();
+            r->u0.clear();
+            cv_done.notify_all();
+            continue;
+        }
+        if (cfg.hbm_budget_bytes && in_use + need > cfg.hbm_budget_bytes) break;
+        pending.pop_front();
+        swp_problem* p = nullptr;
+        swp_status st = swp_create(&r->desc, r->u0.data(), 0, stream, &p);
+        if (st != SWP_OK) {
+            r->status = st;
+            r->state = 2;
+            r->t_done = Clock::now();
+            cv_done.notify_all();
+            continue;
+        }
+        r->prob = p;
+        r->bytes = need;
+        in_use += need;
+        r->u0.clear();
+        r->u0.shrink_to_fit();
+        r->state = 1;
+        r->t_admit = Clock::now();
+        active.push_back(r);
+    }
+}
+
+swp_status swp_server::round()
+{
+    // called without mu: the active list only changes on this thread
+    const double budget_ops = cfg.round_target_ms * 1e-3 * 4.0e11;
+    const double share = budget_ops / (double)active.size();
+    std::vector<swp_problem*> probs;
+    std::vector<int64_t> chunk;
+    for (auto& r : active) {
+        const int64_t left = r->steps_total - r->steps_done;
+        int64_t c = (int64_t)(share / ((double)r->desc.n_points * cost_per_update(r->desc)));
+        c = std::max<int64_t>(1, std::min(c, left));
+        probs.push_back(r->prob);
+        chunk.push_back(c);
+    }
+    const int64_t l0 = swp_batch_kernel_launches(batch);
+    swp_status st = swp_batch_advance(batch, probs.data(), chunk.data(), (int32_t)probs.size(), nullptr,
+                                      cfg.threads);
+    if (st == SWP_OK) st = swp_batch_synchronize(batch);
+    launches += swp_batch_kernel_launches(batch) - l0;
+    rounds++;
+    for (size_t i = 0; i < active.size(); ++i) {
+        if (st != SWP_OK) {
+            active[i]->status = st;
+            active[i]->steps_done = active[i]->steps_total;
+        } else {
+            active[i]->steps_done += chunk[i];
+            point_updates += (double)chunk[i] * (double)active[i]->desc.n_points;
+        }
+    }
+    return st;
+}
+
+void swp_server::retire_finished()
+{
+    std::vector<std::shared_ptr<Request>> keep;
+    std::vector<std::shared_ptr<Request>> done;
+    for (auto& r : active) (r->steps_done >= r->steps_total ? done : keep).push_back(r);
+    for (auto& r : done) {
+        if (r->status == SWP_OK) {
+            r->result.resize(state_bytes(r->desc));
+            r->status = swp_read(r->prob, r->result.data(), r->result.size(), 0);
+        }
+        swp_destroy(r->prob);
+        r->prob = nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    const auto now = Clock::now();
+    for (auto& r : done) {
+        in_use -= r->bytes;
+        r->state = 2;
+        r->t_done = now;
+        completed++;
+        t_last_done = now;
+    }
+    active.swap(keep);
+    if (!done.empty()) cv_done.notify_all();
+}
+
+void swp_server::run()
+{
+    cudaSetDevice(device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            cv_work.wait(lock, [&] { return stop || !pending.empty() || !active.empty(); });
+            if (stop && pending.empty() && active.empty()) return;
+            if (stop) {
+                // shutting down: fail what has not started
+                for (auto& r : pending) {
+                    r->status = SWP_EINVAL;
+                    r->state = 2;
+                    r->t_done = Clock::now();
+                }
+                pending.clear();
+                cv_done.notify_all();
+            }
+            admit();
+        }
+        if (active.empty()) continue;
+        round();
+        retire_finished();
+    }
+}
+
+extern "C" {
+
+swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, swp_server** out)
+{
+    if (!cfg || !out) return SWP_EINVAL;
+    *out = nullptr;
+    if (cfg->max_active <= 0 || !(cfg->round_target_ms > 0) || cfg->threads < 0) return SWP_EINVAL;
+    swp_server* s = new (std::nothrow) swp_server();
+    if (!s) return SWP_ENOMEM;
+    s->cfg = *cfg;
+    s->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return SWP_EDEVICE;
+    }
+    swp_status st = swp_batch_create(cuda_stream, &s->batch);
+    if (st != SWP_OK) {
+        delete s;
+        return st;
+    }
+    s->worker = std::thread([s] { s->run(); });
+    *out = s;
+    return SWP_OK;
+}
+
+swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0_host, int64_t n_steps,
+                             int64_t* request_id)
+{
+    if (!s || !desc || !u0_host || !request_id || n_steps < 1) return SWP_EINVAL;
+    size_t req = 0;
+    swp_status st = swp_required_bytes(desc, &req);   // validates the description
+    if (st != SWP_OK) return st;
+    auto r = std::make_shared<Request>();
+    r->desc = *desc;
+    const size_t nb = state_bytes(*desc);
+    r->u0.assign((const unsigned char*)u0_host, (const unsigned char*)u0_host + nb);
+    r->steps_total = n_steps;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->stop) return SWP_EINVAL;
+        r->id = s->next_id++;
+        if (!s->any_submit) {
+            s->any_submit = true;
+            s->t_first_submit = r->t_submit;
+        }
+        s->pending.push_back(r);
+        s->all[r->id] = r;
+    }
+    s->cv_work.notify_one();
+    *request_id = r->id;
+    return SWP_OK;
+}
+
+swp_status swp_server_poll(swp_server* s, int64_t id, int32_t* done)
+{
+    if (!s || !done) return SWP_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return SWP_EINVAL;
+    *done = it->second->state == 2 ? 1 : 0;
+    return SWP_OK;
+}
+
+swp_status swp_server_wait(swp_server* s, int64_t id, void* dst_host, size_t dst_bytes, double* latency_s)
+{
+    if (!s) return SWP_EINVAL;
+    std::shared_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lock(s->mu);
+        auto it = s->all.find(id);
+        if (it == s->all.end()) return SWP_EINVAL;
+        r = it->second;
+        s->cv_done.wait(lock, [&] { return r->state == 2; });
+        s->all.erase(id);
+    }
+    if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    if (r->status != SWP_OK) return r->status;
+    if (dst_host) {
+        if (dst_bytes < r->result.size()) return SWP_EINVAL;
+        std::memcpy(dst_host, r->result.data(), r->result.size());
+    }
+    return SWP_OK;
+}
+
+swp_status swp_server_stats(swp_server* s, swp_server_statistics* out)
+{
+    if (!s || !out) return SWP_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    out->completed = s->completed;
+    out->rounds = s->rounds;
+    out->kernel_launches = s->launches;
+    out->pending = (int64_t)s->pending.size();
+    out->active = (int64_t)s->active.size();
+    out->device_bytes_in_use = s->in_use;
+    out->point_updates = s->point_updates;
+    out->busy_span_s = s->completed ? std::chrono::duration<double>(s->t_last_done - s->t_first_submit).count() : 0.0;
+    return SWP_OK;
+}
+
+swp_status swp_server_destroy(swp_server* s)
+{
+    if (!s) return SWP_OK;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (auto& r : s->active)
+        if (r->prob) swp_destroy(r->prob);
+    swp_batch_destroy(s->batch);
+    delete s;
+    return SWP_OK;
+}
+
+}  // extern "C"

@@ -364,11 +364,32 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
     return v;
 }
 
+// One (instance, node, phase) item of a batch.
 template <typename R, int EQ>
-__global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
-                                                                              BatchWork w)
+__device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_t p,
+                                           unsigned char* smem_raw)
 {
     constexpr int RAD = Shape<EQ>::RAD;
+    const int H = in.H, n = in.n;
+    const int odd = (int)(p & 1);
+    const int j_lo = p == 0 ? H + 1 : 1;
+    const int j_hi = p < in.Q ? 2 * H - 1 : (p == in.Q ? H + (int)in.r : (int)in.r);
+    R *row0, *row1, *P, *G;
+    smem_rows<R, EQ>(smem_raw, n, row0, row1, P, G);
+    const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
+    const int64_t g0 = xc - n / 2 - RAD;
+    window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
+    __syncthreads();
+    tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
+                       in.bc, in.c);
+    window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
+}
+
+// MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
+                                                                                BatchWork w)
+{
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int task_s, node_s, abort_s;
     for (;;) {
@@ -392,11 +413,9 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_batch_kernel(c
         const int2 tk = w.tasks[t];
         const BatchInst<R>& in = insts[tk.x];
         const int64_t p = tk.y;
-        const int k = node_s, K = in.K, H = in.H, n = in.n;
-        const int odd = (int)(p & 1);
-        const int j_lo = p == 0 ? H + 1 : 1;
-        const int j_hi = p < in.Q ? 2 * H - 1 : (p == in.Q ? H + (int)in.r : (int)in.r);
+        const int k = node_s, K = in.K;
         if (p > 0 && threadIdx.x == 0) {
+            const int odd = (int)(p & 1);
             const int kl = odd ? (k + K - 1) % K : k;
             const int kr = odd ? k : (k + 1) % K;
             const uint32_t need = (uint32_t)p;
@@ -416,15 +435,12 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_batch_kernel(c
         }
         __syncthreads();
         if (abort_s) break;
-        R *row0, *row1, *P, *G;
-        smem_rows<R, EQ>(smem_raw, n, row0, row1, P, G);
-        const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
-        const int64_t g0 = xc - n / 2 - RAD;
-        window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
-        __syncthreads();
-        tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N,
-                           node_near_wall(in.bc, k, K), in.bc, in.c);
-        window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
+        if constexpr (MODE == EULER) {
+            batch_item<R, EULER>(in, k, p, smem_raw);
+        } else {
+            if (in.eq == HEAT) batch_item<R, HEAT>(in, k, p, smem_raw);
+            else batch_item<R, KS>(in, k, p, smem_raw);
+        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) st_release(w.flags + in.flag_off + k, (uint32_t)p + 1);
@@ -476,24 +492,22 @@ int persistent_bps_eq(int n, int threads)
     return nb;
 }
 
-template <typename R, int EQ>
-cudaError_t batch_launch_eq(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
-                            cudaStream_t s)
+template <typename R, int MODE>
+cudaError_t batch_launch_mode(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
+                              cudaStream_t s)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(w.max_n);
-    cudaError_t e = set_smem<R, EQ>((const void*)swept_batch_kernel<R, EQ>, smem);
+    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE>, w.smem_bytes);
     if (e != cudaSuccess) return e;
-    swept_batch_kernel<R, EQ><<<blocks, threads, smem, s>>>(insts, w);
+    swept_batch_kernel<R, MODE><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
     return cudaGetLastError();
 }
 
-template <typename R, int EQ>
-int batch_bps_eq(int max_n, int threads)
+template <typename R, int MODE>
+int batch_bps_mode(size_t smem, int threads)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(max_n);
-    if (set_smem<R, EQ>((const void*)swept_batch_kernel<R, EQ>, smem) != cudaSuccess) return 0;
+    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE>, smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, EQ>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE>, threads, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -562,32 +576,26 @@ template cudaError_t launch_swept_persistent<float>(int, int, float*, float*,
                                                     uint32_t*, unsigned int*, int*, int, int,
                                                     cudaStream_t);
 template <typename R>
-cudaError_t launch_swept_batch(int eq, const BatchInst<R>* insts, const BatchWork& w, int threads,
+cudaError_t launch_swept_batch(int mode, const BatchInst<R>* insts, const BatchWork& w, int threads,
                                int blocks, cudaStream_t s)
 {
-    switch (eq) {
-    case HEAT: return batch_launch_eq<R, HEAT>(insts, w, threads, blocks, s);
-    case KS: return batch_launch_eq<R, KS>(insts, w, threads, blocks, s);
-    default: return batch_launch_eq<R, EULER>(insts, w, threads, blocks, s);
-    }
+    if (mode == EULER) return batch_launch_mode<R, EULER>(insts, w, threads, blocks, s);
+    return batch_launch_mode<R, HEAT>(insts, w, threads, blocks, s);
 }
 
 template <typename R>
-int swept_batch_blocks_per_sm(int eq, int max_n, int threads)
+int swept_batch_blocks_per_sm(int mode, size_t smem_bytes, int threads)
 {
-    switch (eq) {
-    case HEAT: return batch_bps_eq<R, HEAT>(max_n, threads);
-    case KS: return batch_bps_eq<R, KS>(max_n, threads);
-    default: return batch_bps_eq<R, EULER>(max_n, threads);
-    }
+    if (mode == EULER) return batch_bps_mode<R, EULER>(smem_bytes, threads);
+    return batch_bps_mode<R, HEAT>(smem_bytes, threads);
 }
 
 template cudaError_t launch_swept_batch<double>(int, const BatchInst<double>*, const BatchWork&, int,
                                                 int, cudaStream_t);
 template cudaError_t launch_swept_batch<float>(int, const BatchInst<float>*, const BatchWork&, int,
                                                int, cudaStream_t);
-template int swept_batch_blocks_per_sm<double>(int, int, int);
-template int swept_batch_blocks_per_sm<float>(int, int, int);
+template int swept_batch_blocks_per_sm<double>(int, size_t, int);
+template int swept_batch_blocks_per_sm<float>(int, size_t, int);
 template int swept_persistent_blocks_per_sm<double>(int, int, int);
 template int swept_persistent_blocks_per_sm<float>(int, int, int);
 

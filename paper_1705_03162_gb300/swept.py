@@ -24,12 +24,13 @@ HEAT, KS, EULER = 0, 1, 2
 PERIODIC, REFLECTIVE, DIRICHLET = 0, 1, 2
 F64, F32 = 0, 1
 CLASSIC, SWEPT = 0, 1
-LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT = 0, 1, 2
+LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH = 0, 1, 2, 3
 
 _EQ = {"heat": HEAT, "ks": KS, "euler": EULER}
 _BC = {"periodic": PERIODIC, "reflective": REFLECTIVE, "dirichlet": DIRICHLET}
 _SCHEME = {"classic": CLASSIC, "swept": SWEPT}
-_LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT}
+_LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT,
+           "graph": LAUNCH_GRAPH}
 _DTYPE = {"f64": F64, "f32": F32}
 
 # every symbol include/swept.h declares
@@ -40,6 +41,8 @@ ABI_SYMBOLS = (
     "swp_status_str", "swp_last_error", "swp_swept_noalloc",
     "swp_batch_create", "swp_batch_advance", "swp_batch_synchronize", "swp_batch_destroy",
     "swp_batch_kernel_launches", "swp_autotune_width", "swp_tuned_width",
+    "swp_server_create", "swp_server_submit", "swp_server_poll", "swp_server_wait",
+    "swp_server_stats", "swp_server_destroy",
 )
 
 
@@ -60,6 +63,18 @@ class Desc(ctypes.Structure):
         ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("alpha", ctypes.c_double),
         ("gamma", ctypes.c_double), ("left", ctypes.c_double * 3), ("right", ctypes.c_double * 3),
     ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("round_target_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("device_bytes_in_use", ctypes.c_size_t),
+                ("point_updates", ctypes.c_double), ("busy_span_s", ctypes.c_double)]
 
 
 class AdvanceOpts(ctypes.Structure):
@@ -109,6 +124,12 @@ def load_library(path: str = LIB_PATH):
             "swp_batch_kernel_launches": ([P], i64),
             "swp_autotune_width": ([ctypes.POINTER(Desc), vp, i32, i64, ctypes.POINTER(i32)], ctypes.c_int),
             "swp_tuned_width": ([ctypes.POINTER(Desc), ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_server_create": ([ctypes.POINTER(ServerConfig), vp, ctypes.POINTER(P)], ctypes.c_int),
+            "swp_server_submit": ([P, ctypes.POINTER(Desc), vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
+            "swp_server_poll": ([P, i64, ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_server_wait": ([P, i64, vp, sz, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+            "swp_server_stats": ([P, ctypes.POINTER(ServerStats)], ctypes.c_int),
+            "swp_server_destroy": ([P], ctypes.c_int),
             "swp_status_str": ([ctypes.c_int], ctypes.c_char_p),
             "swp_last_error": ([], ctypes.c_char_p),
         }
@@ -328,3 +349,65 @@ def tuned_width(spec: ProblemSpec, dtype: str = "f64") -> int:
     _check(load_library().swp_tuned_width(ctypes.byref(make_desc(spec, dtype)), ctypes.byref(out)),
            "tuned_width")
     return out.value
+
+
+class Server:
+    """Serving loop with continuous batching (scheduler thread in libswept)."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_active: int = 256, round_target_ms: float = 5.0,
+                 threads: int = 0, stream=None):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p(0)
+        cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(threads), float(round_target_ms))
+        handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
+        st = self._lib.swp_server_create(ctypes.byref(cfg), ctypes.c_void_p(handle), ctypes.byref(self._h))
+        if st != OK:
+            raise SweptError(st, "server_create", "invalid configuration or device")
+        self._shapes = {}
+
+    def submit(self, spec: ProblemSpec, u0: np.ndarray, steps: int, dtype: str = "f64") -> int:
+        u0 = np.ascontiguousarray(u0)
+        rid = ctypes.c_int64(0)
+        st = self._lib.swp_server_submit(self._h, ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data,
+                                         int(steps), ctypes.byref(rid))
+        if st != OK:
+            raise SweptError(st, "server_submit", load_library().swp_last_error().decode())
+        self._shapes[rid.value] = (u0.shape, u0.dtype)
+        return rid.value
+
+    def done(self, rid: int) -> bool:
+        d = ctypes.c_int32(0)
+        _check(self._lib.swp_server_poll(self._h, int(rid), ctypes.byref(d)), "server_poll")
+        return bool(d.value)
+
+    def wait(self, rid: int):
+        """(final state as numpy, latency in seconds); raises on a failed request."""
+        shape, dt = self._shapes.pop(rid)
+        out = np.empty(shape, dtype=dt)
+        lat = ctypes.c_double(0.0)
+        st = self._lib.swp_server_wait(self._h, int(rid), out.ctypes.data, out.nbytes, ctypes.byref(lat))
+        if st != OK:
+            raise SweptError(st, "server_wait", f"request {rid} failed")
+        return out, lat.value
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._lib.swp_server_stats(self._h, ctypes.byref(s)), "server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h and self._h.value:
+            self._lib.swp_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -68,7 +68,7 @@ def test_classic_matches_oracle(eq, bc, N, dtype, steps, widths):
 
 
 @pytest.mark.parametrize("eq,bc,N,dtype,steps,widths", CASES)
-@pytest.mark.parametrize("launch", ["per_phase", "persistent"])
+@pytest.mark.parametrize("launch", ["per_phase", "persistent", "graph"])
 def test_swept_matches_oracle_and_classic(eq, bc, N, dtype, steps, widths, launch):
     spec = spec_for(eq, bc, N)
     u0 = state_for(spec, _np(dtype))
@@ -158,6 +158,24 @@ def test_sod_full_time_against_oracle():
     got_s = _gpu(spec, u0, N, "f64", "swept", 256, "persistent")
     assert rel_max(got_c, ref) <= 1e-12 and rel_max(got_s, ref) <= 1e-12
     assert np.array_equal(got_s, got_c)
+
+
+@pytest.mark.parametrize("eq,bc", [("heat", "periodic"), ("heat", "reflective"), ("ks", "periodic"),
+                                   ("euler", "dirichlet")])
+def test_graph_replay_matches_stream_launches(eq, bc):
+    """Graph launches (captured once, replayed) give the stream launches' bits,
+    on repeated identical advances and with the starting row alternating."""
+    spec = spec_for(eq, bc, 2048)
+    u0 = state_for(spec)
+    with S.Problem(spec, u0) as a, S.Problem(spec, u0) as b:
+        for steps, n in ((33, 64), (33, 64), (20, 128), (33, 64), (7, 64)):
+            a.advance(steps, "swept", n, "per_phase")
+            b.advance(steps, "swept", n, "graph")
+            assert np.array_equal(a.read(), b.read())
+        for steps in (5, 5, 6):
+            a.advance(steps, "classic")
+            b.advance(steps, "classic", launch="graph")
+            assert np.array_equal(a.read(), b.read())
 
 
 def test_invalid_node_width_rejected():
