@@ -33,7 +33,7 @@ from paper_1705_03162_gb300 import inputs as I  # noqa: E402
 
 DEFAULT_WORKLOAD = {
     "eq": "ks", "n_points": 1 << 20, "steps": 10_000, "dtype": "f64",
-    "points_per_block": 512, "launch": "per_phase", "threads": 0,
+    "points_per_block": 1024, "launch": "per_phase", "threads": 256,
 }
 METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served solve latency"
 UNIT = "G point-updates/s"
@@ -50,9 +50,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # a hash of the kernel sources it was taken on; reported as null once the
 # sources change.
 NCU_TRAFFIC = {
-    # profiles/swept_phase_kernel_ks_n512.md: dram__bytes_read.sum + dram__bytes_write.sum of a
+    # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
-    "swept_phase_kernel<double,KS> n=512": {"src": "f50502abd4fe5fde", "bytes_per_launch": 16784128},
+    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "95810c9ff89163be", "bytes_per_launch": 16784640},
 }
 
 
@@ -377,8 +377,9 @@ def run_gpu(args, wl):
     prob = S.Problem(spec, u0_dev)
 
     def one(scheme):
-        return prob.advance(steps, scheme, wl["points_per_block"] if scheme == "swept" else 0,
-                            wl["launch"], wl["threads"])
+        if scheme == "classic":
+            return prob.advance(steps, "classic")
+        return prob.advance(steps, "swept", wl["points_per_block"], wl["launch"], wl["threads"])
 
     def timed(scheme, k):
         """k solves, each from the initial state with L2 flushed before it;
@@ -420,6 +421,21 @@ def run_gpu(args, wl):
     torch.cuda.synchronize()
     dist.barrier()
     t_classic = dist.max(t_classic)
+    # classic with its launch sequence as a CUDA graph (captured in warm-up)
+    prob.write(u0_dev)
+    prob.advance(steps, "classic", launch="graph")
+    torch.cuda.synchronize()
+    t_classic_graph = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        prob.write(u0_dev)
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        prob.advance(steps, "classic", launch="graph")
+        b2.record()
+        torch.cuda.synchronize()
+        t_classic_graph += a.elapsed_time(b2) / 1e3
+    t_classic_graph = dist.max(t_classic_graph)
     clk = clocks.stop()
 
     # end to end through the C ABI with host buffers (pinned): H2D of the
@@ -439,6 +455,7 @@ def run_gpu(args, wl):
     upd = float(N) * steps * args.steps * world
     value = upd / t_swept / 1e9
     classic_value = upd / t_classic / 1e9
+    classic_graph_value = upd / t_classic_graph / 1e9
     e2e_value = upd / t_e2e / 1e9
 
     # roofline of the dominant kernel (the swept phase kernel, FP64-pipe bound)
@@ -447,7 +464,7 @@ def run_gpu(args, wl):
     flops_per_launch = float(N) * steps * KS_FLOPS_PER_UPDATE / launches_per_solve
     achieved = flops_per_launch / avg_launch_s / 1e12
     ops_rate = float(N) * steps * args.steps * KS_FP64_OPS_PER_UPDATE / t_swept / 1e12
-    key = f"swept_phase_kernel<double,KS> n={wl['points_per_block']}"
+    key = f"swept_phase_kernel<double,KS> n={wl['points_per_block']} threads={wl['threads']}"
     traffic = None
     rec = NCU_TRAFFIC.get(key)
     if rec and rec.get("src") == _kernel_src_hash():
@@ -467,7 +484,9 @@ def run_gpu(args, wl):
                    "l2": "256 MB buffer written before every timed solve (state 16 MB is L2-resident within a solve)"},
         "classic": {"value": classic_value, "ms_per_step": t_classic / args.steps * 1e3,
                     "kernel_launches_per_solve": launches_classic / args.steps,
-                    "swept_speedup": classic_value and value / classic_value},
+                    "swept_speedup": classic_value and value / classic_value,
+                    "graph_value": classic_graph_value,
+                    "swept_speedup_vs_graph": value / classic_graph_value},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
                 "d2h_bytes_per_step": int(u0_host.nbytes)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -500,7 +519,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--points-per-block", type=int, default=DEFAULT_WORKLOAD["points_per_block"])
     ap.add_argument("--launch", choices=["per_phase", "persistent", "auto"], default=DEFAULT_WORKLOAD["launch"])
-    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=DEFAULT_WORKLOAD["threads"])
     ap.add_argument("--timesteps", type=int, default=DEFAULT_WORKLOAD["steps"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

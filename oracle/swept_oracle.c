@@ -128,7 +128,7 @@ int orc_swept(const orc_problem* pb, int32_t dtype, void* state, int64_t steps, 
  * hand-worked states (FP64).  q: conserved (rho, rho u, E) triples. */
 double orc_euler_pressure_f64(const double* q, double gamma)
 {
-    return euler_pressure_f64(q[0], q[1], q[2], gamma - 1.0, NULL);
+    return euler_pressure_f64(q[0], q[1], q[2], gamma - 1.0, NULL, NULL);
 }
 
 /* q: 4 cells (a-1, a, b, b+1) x 3; outputs the reconstructed left and right
@@ -136,7 +136,7 @@ double orc_euler_pressure_f64(const double* q, double gamma)
 int orc_euler_reconstruct_f64(const double* q, double gamma, double* ql, double* qr)
 {
     double gm1 = gamma - 1.0, p[4];
-    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL);
+    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL, NULL);
     euler_reconstruct_f64(q + 3, q + 6, p[0], p[1], p[2], p[3], ql, qr);
     return ORC_OK;
 }
@@ -146,7 +146,7 @@ int orc_euler_interface_f64(const double* q, double gamma, double* G)
 {
     double gm1 = gamma - 1.0, ggm1 = gamma * (gamma - 1.0);
     double p[4];
-    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL);
+    for (int k = 0; k < 4; ++k) p[k] = euler_pressure_f64(q[3 * k], q[3 * k + 1], q[3 * k + 2], gm1, NULL, NULL);
     euler_interface_f64(q + 3, q + 6, p[0], p[1], p[2], p[3], gm1, ggm1, G);
     return ORC_OK;
 }

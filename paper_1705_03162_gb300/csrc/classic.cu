@@ -1,8 +1,10 @@
 // Classic decomposition (arXiv:1705.03162 Section 5.1): one kernel launch per
 // sub-timestep, every point advanced from the previous sub-timestep's full
-// array in global memory.  GB300 form: each block stages its tile plus a
-// stencil halo (boundary condition applied while loading) in shared memory
-// with coalesced loads, then evaluates the shared point update of scheme.cuh.
+// array in global memory.  GB300 forms: heat and KS stream 16-byte vectors
+// with neighbours exchanged by warp shuffle (bandwidth form); otherwise each
+// block stages its tile plus a stencil halo (boundary condition applied while
+// loading) in shared memory.  Both evaluate the shared point update of
+// scheme.cuh.
 // Euler evaluates each interface flux once per tile (P per cell, G per
 // interface) instead of twice per cell.
 #include "launch.h"
@@ -53,8 +55,7 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
         R* G = P + SW;              // G[v][l]: interface between tile cells l-1 and l
         const int GW = TILE + 1;
         for (int s = threadIdx.x; s < SW; s += T) {
-            R u;
-            P[s] = euler_pressure(sm[s], sm[SW + s], sm[2 * SW + s], c.gm1, u);
+            P[s] = euler_pressure(sm[s], sm[SW + s], sm[2 * SW + s], c.gm1);
         }
         __syncthreads();
         for (int l = threadIdx.x; l < GW; l += T) {
@@ -92,10 +93,111 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bandwidth form for heat and KS (N a multiple of the vector width): every
+// thread moves 16-byte vectors (float4 / double2), U of them in flight (U = 4
+// when the grid still covers every SM twice, else 1); stencil neighbours come from the adjacent lanes by warp shuffle, and
+// only the first and last lane of a warp row load a halo vector.
+// ---------------------------------------------------------------------------
+template <typename R> struct Vec16;
+template <> struct Vec16<float> {
+    using T = float4;
+    static constexpr int W = 4;
+};
+template <> struct Vec16<double> {
+    using T = double2;
+    static constexpr int W = 2;
+};
+
+
+template <typename R>
+__device__ __forceinline__ void vec_to(const typename Vec16<R>::T& v, R* a)
+{
+    const R* p = reinterpret_cast<const R*>(&v);
+#pragma unroll
+    for (int i = 0; i < Vec16<R>::W; ++i) a[i] = p[i];
+}
+
+// The VW values of vector vi of a level (vi may lie outside [0, nvec): the
+// boundary condition supplies them).
+template <typename R>
+__device__ __forceinline__ void vec_load_bc(const R* arr, int64_t vi, int64_t nvec, int64_t N, int bc,
+                                            const Coefs<R>& c, R* a)
+{
+    constexpr int VW = Vec16<R>::W;
+    using T = typename Vec16<R>::T;
+    if (vi >= 0 && vi < nvec) {
+        vec_to<R>(reinterpret_cast<const T*>(arr)[vi], a);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < VW; ++i) a[i] = bc_load(arr, vi * VW + i, N, bc, 0, c);
+}
+
+template <typename R, int EQ, int U>
+__global__ void __launch_bounds__(256) classic_vec_kernel(const R* __restrict__ src, const R* base,
+                                                          R* out, int64_t N, int stage, int bc,
+                                                          Coefs<R> c)
+{
+    constexpr int VW = Vec16<R>::W;
+    using T = typename Vec16<R>::T;
+    const int lane = threadIdx.x & 31;
+    const int64_t nvec = N / VW;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t row0 = warp_global * (32 * U);
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t vi = row0 + u * 32 + lane;
+        if (vi < nvec) v[u] = reinterpret_cast<const T*>(src)[vi];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t vi = row0 + u * 32 + lane;
+        R a[3 * VW];   // left vector, own vector, right vector
+        vec_to<R>(v[u], a + VW);
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+            a[i] = __shfl_up_sync(0xffffffffu, a[VW + i], 1);
+            a[2 * VW + i] = __shfl_down_sync(0xffffffffu, a[VW + i], 1);
+        }
+        if (vi >= nvec) continue;
+        if (lane == 0 || vi == 0) vec_load_bc<R>(src, vi - 1, nvec, N, bc, c, a);
+        if (lane == 31 || vi == nvec - 1) vec_load_bc<R>(src, vi + 1, nvec, N, bc, c, a + 2 * VW);
+        R o[VW];
+        if constexpr (EQ == HEAT) {
+#pragma unroll
+            for (int i = 0; i < VW; ++i) o[i] = heat_point(a[VW + i - 1], a[VW + i], a[VW + i + 1], c.fo);
+        } else {
+            R b[VW];
+            vec_to<R>(reinterpret_cast<const T*>(base)[vi], b);
+#pragma unroll
+            for (int i = 0; i < VW; ++i)
+                o[i] = ks_point(a[VW + i - 2], a[VW + i - 1], a[VW + i], a[VW + i + 1], a[VW + i + 2], b[i],
+                                c.a1[stage], c.a4[stage], c.beta[stage], c.gam[stage]);
+        }
+        reinterpret_cast<T*>(out)[vi] = *reinterpret_cast<const T*>(o);
+    }
+}
+
 template <typename R, int EQ>
 cudaError_t classic_launch_eq(int bc, const R* src, const R* base, R* out, int64_t N, int stage,
                               const Coefs<R>& c, int threads, cudaStream_t s)
 {
+    if constexpr (EQ != EULER) {
+        constexpr int VW = Vec16<R>::W;
+        if (N % VW == 0 && N / VW >= 32) {
+            const int64_t nvec = N / VW;
+            const int64_t blocks4 = (nvec + 4 * (int64_t)threads - 1) / (4 * (int64_t)threads);
+            if (blocks4 >= 2 * 152) {
+                classic_vec_kernel<R, EQ, 4><<<(unsigned)blocks4, threads, 0, s>>>(src, base, out, N, stage, bc, c);
+            } else {
+                const int64_t blocks1 = (nvec + threads - 1) / threads;
+                classic_vec_kernel<R, EQ, 1><<<(unsigned)blocks1, threads, 0, s>>>(src, base, out, N, stage, bc, c);
+            }
+            return cudaGetLastError();
+        }
+    }
     constexpr int RAD = EQ == HEAT ? 1 : 2;
     constexpr int NV = EQ == EULER ? 3 : 1;
     const int tile = threads * kClassicPointsPerThread;

@@ -21,6 +21,7 @@ template <> struct Fp<double> {
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
     static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
     static __device__ __forceinline__ double abs(double a) { return fabs(a); }
 };
@@ -30,6 +31,7 @@ template <> struct Fp<float> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
     static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
     static __device__ __forceinline__ float abs(float a) { return fabsf(a); }
 };
@@ -84,13 +86,22 @@ __device__ __forceinline__ R ks_point(R vmm, R vm, R v0, R vp, R vpp, R base,
 // Euler (Appendix C).  Conserved Q = (rho, rho u, E), E total energy per volume.
 // ---------------------------------------------------------------------------
 
-// Velocity and pressure, Eq. EulerP: u = (rho u)/rho, P = (gamma-1)(E - (rho u) u / 2).
+// Velocity and pressure, Eq. EulerP: u = (rho u)/rho, P = (gamma-1)(E - (rho u) u / 2),
+// dividing by rho as a multiplication by the correctly rounded 1/rho (ir).
 template <typename R>
-__device__ __forceinline__ R euler_pressure(R r, R m, R E, R gm1, R& u)
+__device__ __forceinline__ R euler_pressure(R r, R m, R E, R gm1, R& u, R& ir)
 {
     using F = Fp<R>;
-    u = F::div(m, r);
+    ir = F::rcp(r);
+    u = F::mul(m, ir);
     return F::mul(gm1, F::fma(F::mul(R(-0.5), m), u, E));
+}
+
+template <typename R>
+__device__ __forceinline__ R euler_pressure(R r, R m, R E, R gm1)
+{
+    R u, ir;
+    return euler_pressure(r, m, E, gm1, u, ir);
 }
 
 // min(num/den, 1) for num, den nonzero with the same sign.  When
@@ -141,25 +152,26 @@ __device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], 
 // F(Q) = (rho u, rho u^2 + P, u (E + P)) (Eq. EulerF) and spectral radius
 // r_sp = sqrt(gamma (gamma-1) (e_sp - u_sp^2/2)) + |u_sp| from sqrt(rho)-weighted
 // Roe averages of u and of e = E/rho (gamma P_sp / rho_sp with
-// P_sp = (gamma-1) rho_sp (e_sp - u_sp^2/2)).
+// P_sp = (gamma-1) rho_sp (e_sp - u_sp^2/2)).  Divisions by rho and by the
+// weight sum are multiplications by correctly rounded reciprocals.
 template <typename R>
 __device__ __forceinline__ void euler_flux(const R ql[3], const R qr[3], R gm1, R ggm1, R G[3])
 {
     using F = Fp<R>;
-    R ul, ur;
-    R pl = euler_pressure(ql[0], ql[1], ql[2], gm1, ul);
-    R pr = euler_pressure(qr[0], qr[1], qr[2], gm1, ur);
+    R ul, ur, irl, irr;
+    R pl = euler_pressure(ql[0], ql[1], ql[2], gm1, ul, irl);
+    R pr = euler_pressure(qr[0], qr[1], qr[2], gm1, ur, irr);
     R fl1 = F::fma(ql[1], ul, pl);
     R fl2 = F::mul(ul, F::add(ql[2], pl));
     R fr1 = F::fma(qr[1], ur, pr);
     R fr2 = F::mul(ur, F::add(qr[2], pr));
     R sl = F::sqrt(ql[0]);
     R sr = F::sqrt(qr[0]);
-    R w = F::add(sl, sr);
-    R usp = F::div(F::fma(sl, ul, F::mul(sr, ur)), w);
-    R el = F::div(ql[2], ql[0]);
-    R er = F::div(qr[2], qr[0]);
-    R esp = F::div(F::fma(sl, el, F::mul(sr, er)), w);
+    R iw = F::rcp(F::add(sl, sr));
+    R usp = F::mul(F::fma(sl, ul, F::mul(sr, ur)), iw);
+    R el = F::mul(ql[2], irl);
+    R er = F::mul(qr[2], irr);
+    R esp = F::mul(F::fma(sl, el, F::mul(sr, er)), iw);
     R c2 = F::mul(ggm1, F::fma(F::mul(R(-0.5), usp), usp, esp));
     R rsp = F::add(F::sqrt(c2), F::abs(usp));
     G[0] = F::fma(rsp, F::sub(ql[0], qr[0]), F::add(qr[1], ql[1]));

@@ -167,8 +167,7 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
 #pragma unroll
                         for (int v = 0; v < 3; ++v)
                             qs[k][v] = wall_fetch(src, W, q, k - 2, v, g0, N, bc, c);
-                        R u;
-                        p[k] = euler_pressure(qs[k][0], qs[k][1], qs[k][2], c.gm1, u);
+                        p[k] = euler_pressure(qs[k][0], qs[k][1], qs[k][2], c.gm1);
                     }
                     R gm[3], gp[3];
                     euler_interface(qs[1], qs[2], p[0], p[1], p[2], p[3], c.gm1, c.ggm1, gm);
@@ -184,8 +183,7 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
                 const int GW = W + 1;
                 for (int t = threadIdx.x; t < cnt + 4; t += T) {
                     const int s = lo - 2 + t;
-                    R u;
-                    P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1, u);
+                    P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1);
                 }
                 __syncthreads();
                 for (int t = threadIdx.x; t <= cnt; t += T) {

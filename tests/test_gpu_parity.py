@@ -67,6 +67,19 @@ def test_classic_matches_oracle(eq, bc, N, dtype, steps, widths):
     assert np.array_equal(got, ref), "classic is not bit-identical to the oracle"
 
 
+@pytest.mark.parametrize("eq,bc,N,dtype", [("heat", "periodic", 4993, "f64"), ("heat", "reflective", 4993, "f32"),
+                                           ("ks", "periodic", 4998, "f32"), ("ks", "periodic", 4999, "f64"),
+                                           ("heat", "periodic", 64, "f32"), ("ks", "periodic", 130, "f64")])
+def test_classic_sizes_off_the_vector_width(eq, bc, N, dtype):
+    """N not a multiple of the 16-byte vector width (or too small) takes the
+    shared-memory classic kernel; both forms must agree with the oracle."""
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec, _np(dtype))
+    ref = _oracle(spec, u0, 97)
+    got = _gpu(spec, u0, 97, dtype, "classic")
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("eq,bc,N,dtype,steps,widths", CASES)
 @pytest.mark.parametrize("launch", ["per_phase", "persistent", "graph"])
 def test_swept_matches_oracle_and_classic(eq, bc, N, dtype, steps, widths, launch):
