@@ -90,10 +90,15 @@ typedef enum {
                                    nodes synchronise at kernel boundaries */
     SWP_LAUNCH_PERSISTENT = 2,  /* one kernel for the whole advance; each node
                                    waits (bounded) on its two neighbours' flags */
-    SWP_LAUNCH_GRAPH = 3        /* the per-phase (swept) or per-sub-step (classic)
+    SWP_LAUNCH_GRAPH = 3,       /* the per-phase (swept) or per-sub-step (classic)
                                    launches as a CUDA graph, captured on first use
                                    for (scheme, n_steps, width, threads) and
                                    replayed afterwards */
+    SWP_LAUNCH_REGISTER = 4     /* the paper's Register variant (Section 5.1):
+                                   one warp per node of 32 points, levels in
+                                   registers, neighbours by warp shuffle; one
+                                   kernel per phase; periodic heat and KS only
+                                   (points_per_block 32 or 0) */
 } swp_launch;
 
 typedef struct {

@@ -234,6 +234,28 @@ SweptPlan plan_swept(const swp_problem* p, int64_t steps, int n)
 }
 
 template <typename R>
+swp_status run_swept_register(swp_problem* p, const SweptPlan& s, int threads)
+{
+    R* A = (R*)p->rows[p->cur];
+    R* B = (R*)p->rows[1 - p->cur];
+    const Coefs<R>& c = coefs_of<R>(p);
+    for (int64_t ph = 0; ph < s.n_phases; ++ph) {
+        PhaseGeom g;
+        g.N = p->N;
+        g.n = s.n;
+        g.H = s.H;
+        g.K = s.K;
+        g.j_lo = ph == 0 ? s.H + 1 : 1;
+        g.j_hi = ph < s.Q ? 2 * s.H - 1 : (ph == s.Q ? s.H + (int)s.r : (int)s.r);
+        g.odd = (int)(ph & 1);
+        cudaError_t e = launch_swept_register<R>(p->desc.eq, A, B, g, c, threads, p->stream);
+        p->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "register swept launch");
+    }
+    return SWP_OK;
+}
+
+template <typename R>
 swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads)
 {
     R* A = (R*)p->rows[p->cur];
@@ -407,6 +429,21 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
             return run_graph<R>(p, steps, SWP_CLASSIC, 0, thr, nullptr);
         }
         return run_classic<R>(p, steps, o.threads);
+    }
+    if (o.launch == SWP_LAUNCH_REGISTER) {
+        if (p->desc.eq == SWP_EULER || p->desc.bc != SWP_BC_PERIODIC)
+            return fail(SWP_EUNSUPPORTED, "the register variant runs periodic heat and KS");
+        if (o.points_per_block != 0 && o.points_per_block != 32)
+            return fail(SWP_EINVAL, "the register variant's node is one warp: points_per_block 32 (or 0)");
+        if (p->N % 32 || p->N < 64) return fail(SWP_EINVAL, "the register variant needs n_points a multiple of 32, >= 64");
+        const int thr = o.threads == 0 ? 256 : o.threads;
+        if (thr < 32 || thr > 256 || thr % 32) return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, 256]");
+        const SweptPlan s = plan_swept(p, steps, 32);
+        if (s.T == 0) return SWP_OK;
+        swp_status st = run_swept_register<R>(p, s, thr);
+        if (st != SWP_OK) return st;
+        if (s.top & 1) p->cur = 1 - p->cur;
+        return SWP_OK;
     }
     int n = o.points_per_block;
     if (n == 0) {

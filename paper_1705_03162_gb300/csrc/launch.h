@@ -38,6 +38,12 @@ template <typename R>
 cudaError_t launch_swept_phase(int eq, int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
                                int threads, cudaStream_t s);
 
+// Register variant of one phase (heat / KS, periodic): node width 32, one
+// warp per node, levels in registers with warp-shuffle neighbours.
+template <typename R>
+cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
+                                  int threads, cudaStream_t s);
+
 // Whole advance in one persistent launch: blocks claim (phase, node) items in
 // order and wait, with a bounded spin, for the two neighbouring nodes of the
 // previous phase.  flags[K] hold completed-phase counts offset by flag_base;

@@ -24,13 +24,13 @@ HEAT, KS, EULER = 0, 1, 2
 PERIODIC, REFLECTIVE, DIRICHLET = 0, 1, 2
 F64, F32 = 0, 1
 CLASSIC, SWEPT = 0, 1
-LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH = 0, 1, 2, 3
+LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH, LAUNCH_REGISTER = 0, 1, 2, 3, 4
 
 _EQ = {"heat": HEAT, "ks": KS, "euler": EULER}
 _BC = {"periodic": PERIODIC, "reflective": REFLECTIVE, "dirichlet": DIRICHLET}
 _SCHEME = {"classic": CLASSIC, "swept": SWEPT}
 _LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT,
-           "graph": LAUNCH_GRAPH}
+           "graph": LAUNCH_GRAPH, "register": LAUNCH_REGISTER}
 _DTYPE = {"f64": F64, "f32": F32}
 
 # every symbol include/swept.h declares

@@ -191,6 +191,34 @@ def test_graph_replay_matches_stream_launches(eq, bc):
             assert np.array_equal(a.read(), b.read())
 
 
+@pytest.mark.parametrize("eq,N,dtype,steps", [("ks", 4992, "f64", 301), ("ks", 4992, "f32", 150),
+                                            ("heat", 4992, "f64", 203), ("heat", 96, "f32", 61),
+                                            ("ks", 64, "f64", 9)])
+def test_register_variant_matches_oracle(eq, N, dtype, steps):
+    """The Register variant (one warp per node of 32 points, levels in
+    registers) gives the oracle's bits, remainders and a two-node ring included."""
+    spec = spec_for(eq, "periodic", N)
+    u0 = state_for(spec, _np(dtype))
+    ref = _oracle(spec, u0, steps)
+    for threads in (32, 256):
+        with S.Problem(spec, u0, dtype) as p:
+            p.advance(steps, "swept", 0, "register", threads)
+            assert np.array_equal(p.read(), ref)
+
+
+def test_register_variant_rejects_unsupported():
+    spec = spec_for("heat", "reflective", 256)
+    with S.Problem(spec, state_for(spec)) as p:
+        with pytest.raises(S.SweptError) as e:
+            p.advance(5, "swept", 0, "register")
+        assert e.value.status == S.EUNSUPPORTED
+    spec = spec_for("ks", "periodic", 256)
+    with S.Problem(spec, state_for(spec)) as p:
+        with pytest.raises(S.SweptError) as e:
+            p.advance(5, "swept", 64, "register")
+        assert e.value.status == S.EINVAL
+
+
 def test_invalid_node_width_rejected():
     spec = spec_for("ks", "periodic", 1000)
     with S.Problem(spec, state_for(spec)) as p:
