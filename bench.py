@@ -511,6 +511,76 @@ def run_gpu(args, wl):
     dist.close()
 
 
+
+# ---------------------------------------------------------------------------
+# optional modes: size sweep and classic bandwidth
+# ---------------------------------------------------------------------------
+def _time_solve(prob, u0d, steps, scheme, n=0, launch="per_phase", threads=0, reps=2):
+    import torch
+    prob.advance(min(steps, 20), scheme, n, launch, threads)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        prob.write(u0d)
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        prob.advance(steps, scheme, n, launch, threads)
+        b2.record()
+        torch.cuda.synchronize()
+        best = min(best, a.elapsed_time(b2) / 1e3)
+    return best
+
+
+def run_sweep(steps: int = 2000):
+    """Swept (shared, best node width and launch), Register variant and classic
+    (CUDA graph) for heat and KS at N = 2^11..2^20, FP64: one JSON line each."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    for eq in ("ks", "heat"):
+        for e in range(11, 21):
+            N = 1 << e
+            spec, u0 = _spec_ic(eq, N)
+            u0d = torch.from_numpy(u0).cuda()
+            with S.Problem(spec, u0d) as p:
+                classic = N * steps / _time_solve(p, u0d, steps, "classic", launch="graph") / 1e9
+                reg = N * steps / _time_solve(p, u0d, steps, "swept", 0, "register", 64) / 1e9
+                best, cfg = 0.0, None
+                for n in (64, 128, 256, 512, 1024):
+                    if N % n or N // n < 2:
+                        continue
+                    for launch in ("per_phase", "graph"):
+                        r = N * steps / _time_solve(p, u0d, steps, "swept", n, launch) / 1e9
+                        if r > best:
+                            best, cfg = r, {"points_per_block": n, "launch": launch}
+            print(json.dumps({"sweep": eq, "n_points": N, "timesteps": steps, "dtype": "f64", "unit": UNIT,
+                              "classic_graph": classic, "swept": best, "swept_config": cfg,
+                              "register": reg, "swept_speedup": best / classic}), flush=True)
+
+
+def run_bandwidth(steps: int = 200):
+    """Classic FP32 heat and KS at N = 2^26 (arrays far beyond L2): achieved
+    algorithmic HBM bandwidth against the measured copy peak."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    peak = 6790.3
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        pass
+    N = 1 << 26
+    for eq, bytes_per_update in (("heat", 8), ("ks", 20)):
+        spec, u0 = _spec_ic(eq, N, np.float32)
+        u0d = torch.from_numpy(u0).cuda()
+        with S.Problem(spec, u0d, "f32") as p:
+            t = _time_solve(p, u0d, steps if eq == "heat" else steps // 2, "classic", launch="graph")
+        st = steps if eq == "heat" else steps // 2
+        gbs = bytes_per_update * N * st / t / 1e9
+        print(json.dumps({"bandwidth": f"classic {eq} FP32 N=2^26", "timesteps": st,
+                          "value": N * st / t / 1e9, "unit": UNIT, "algorithmic_gbs": gbs,
+                          "bytes_per_update": bytes_per_update, "hbm_peak_gbs": peak,
+                          "frac": gbs / peak}), flush=True)
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +592,8 @@ def main():
     ap.add_argument("--threads", type=int, default=DEFAULT_WORKLOAD["threads"])
     ap.add_argument("--timesteps", type=int, default=DEFAULT_WORKLOAD["steps"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="print the per-size sweep lines instead")
+    ap.add_argument("--bandwidth", action="store_true", help="print the classic FP32 bandwidth lines instead")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the served, batched and FP32-error measurements")
     args = ap.parse_args()
@@ -531,6 +603,13 @@ def main():
               threads=args.threads, steps=args.timesteps)
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.sweep or args.bandwidth:
+        from paper_1705_03162_gb300 import swept as S
+        S.load_library()
+        if args.sweep:
+            run_sweep()
+        if args.bandwidth:
+            run_bandwidth()
     else:
         run_gpu(args, wl)
 

@@ -162,15 +162,19 @@ swp_status check_width(const swp_problem* p, int n)
     return SWP_OK;
 }
 
-// Default node width: enough nodes to cover every SM twice when N allows,
-// at most 1024 points (512 for Euler), at least 32.
+// Default node width, from the widths measured fastest on GB300 for single
+// problems: about N / 1024 points, at least 64 (heat) or 128 (KS, Euler) and
+// at most 1024 (Euler 512); the nearest width that divides N, is a multiple
+// of 4 rad and fits shared memory.
 int default_width(const swp_problem* p)
 {
     const int step = 4 * p->rad;
+    const int lo = p->desc.eq == SWP_HEAT ? 64 : 128;
     const int cap = p->desc.eq == SWP_EULER ? 512 : 1024;
-    int64_t target = p->N / (2 * (int64_t)(p->sms > 0 ? p->sms : 152));
+    int64_t target = p->N / 1024;
+    if (target < lo) target = lo;
     if (target > cap) target = cap;
-    if (target < 32) target = 32;
+    if (target > p->N / 2) target = p->N / 2;
     for (int64_t n = target; n >= step; --n)
         if (n % step == 0 && p->N % n == 0 && check_width(p, (int)n) == SWP_OK) return (int)n;
     for (int64_t n = target + 1; n <= cap && n <= p->N; ++n)

@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
             const int64_t i = t0 + l;
             if (i >= N) break;
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
-                out[v * N + i] = euler_update(G[v * GW + l + 1], G[v * GW + l], base[v * N + i], kh);
+            for (int v = 0; v < 3; ++v) {
+                const R b = stage == 0 ? sm[v * SW + RAD + l] : base[v * N + i];   // predictor: base = source
+                out[v * N + i] = euler_update(G[v * GW + l + 1], G[v * GW + l], b, kh);
+            }
         }
     } else {
         for (int l = threadIdx.x; l < TILE; l += T) {
@@ -86,7 +88,8 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
             if constexpr (EQ == HEAT) {
                 out[i] = heat_point(sm[s - 1], sm[s], sm[s + 1], c.fo);
             } else {
-                out[i] = ks_point(sm[s - 2], sm[s - 1], sm[s], sm[s + 1], sm[s + 2], base[i],
+                const R b = stage == 0 ? sm[s] : base[i];   // predictor: base = source
+                out[i] = ks_point(sm[s - 2], sm[s - 1], sm[s], sm[s + 1], sm[s + 2], b,
                                   c.a1[stage], c.a4[stage], c.beta[stage], c.gam[stage]);
             }
         }
@@ -170,7 +173,12 @@ __global__ void __launch_bounds__(256) classic_vec_kernel(const R* __restrict__ 
             for (int i = 0; i < VW; ++i) o[i] = heat_point(a[VW + i - 1], a[VW + i], a[VW + i + 1], c.fo);
         } else {
             R b[VW];
-            vec_to<R>(reinterpret_cast<const T*>(base)[vi], b);
+            if (stage == 0) {   // predictor: the base is the source vector itself
+#pragma unroll
+                for (int i = 0; i < VW; ++i) b[i] = a[VW + i];
+            } else {
+                vec_to<R>(reinterpret_cast<const T*>(base)[vi], b);
+            }
 #pragma unroll
             for (int i = 0; i < VW; ++i)
                 o[i] = ks_point(a[VW + i - 2], a[VW + i - 1], a[VW + i], a[VW + i + 1], a[VW + i + 2], b[i],
