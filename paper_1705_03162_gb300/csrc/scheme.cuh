@@ -64,22 +64,21 @@ __device__ __forceinline__ R heat_point(R tm, R t0, R tp, R fo)
 // RKf): out = base + h f(v), base = u^m, h = dt/2 (predictor) or dt (final).
 // The Laplacian (1, -2, 1)/dx^2 and the fourth difference (1, -4, 6, -4, 1)/dx^4
 // combine into one five-point stencil with weights a4 (v++, v--),
-// beta = a2 - 4 a4 (v+, v-) and gam = 6 a4 - 2 a2 (v), so
-//   h f = a1 (v+^2 - v-^2) + a4 (v++ + v--) + beta (v+ + v-) + gam v,
-// with a1 = -h/(4dx), a2 = -h/dx^2, a4 = -h/dx^4.  Eight FP operations.
+// beta = a2 - 4 a4 (v+, v-) and gam = 6 a4 - 2 a2 (v); the nonlinear term
+// a1 (v+^2 - v-^2) = a1 (v+ - v-)(v+ + v-) shares the factor v+ + v-, so
+//   h f = gam v + a4 (v++ + v--) + (beta + a1 (v+ - v-)) (v+ + v-),
+// with a1 = -h/(4dx), a2 = -h/dx^2, a4 = -h/dx^4.  Seven FP operations; the
+// dependent chain is three deep.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ R ks_point(R vmm, R vm, R v0, R vp, R vpp, R base,
                                       R a1, R a4, R beta, R gam)
 {
     using F = Fp<R>;
-    // summed into base in the order gam, beta, a4, a1 terms: the first three
-    // need no product of neighbours, so the dependent chain is four deep
-    R b = F::fma(vp, vp, -F::mul(vm, vm));
+    const R t = F::fma(a1, F::sub(vp, vm), beta);
     R acc = F::fma(gam, v0, base);
-    acc = F::fma(beta, F::add(vp, vm), acc);
     acc = F::fma(a4, F::add(vpp, vmm), acc);
-    return F::fma(a1, b, acc);
+    return F::fma(t, F::add(vp, vm), acc);
 }
 
 // ---------------------------------------------------------------------------
