@@ -103,18 +103,28 @@ __device__ __forceinline__ R euler_pressure(R r, R m, R E, R gm1)
     return euler_pressure(r, m, E, gm1, u, ir);
 }
 
+// Sign and magnitude tests on the IEEE bit patterns (integer pipe; GB300's
+// FP64 pipe would spend a full slot on each comparison).  Equal to the
+// floating-point comparisons for every non-NaN value.
+__device__ __forceinline__ uint64_t fbits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ uint32_t fbits(float x) { return (uint32_t)__float_as_uint(x); }
+
+// (a > 0 && b > 0) || (a < 0 && b < 0): both nonzero, equal sign bits
+template <typename R>
+__device__ __forceinline__ bool same_sign(R a, R b)
+{
+    const auto ua = fbits(a), ub = fbits(b);
+    constexpr int top = 8 * sizeof(R) - 1;
+    return (ua << 1) != 0 && (ub << 1) != 0 && ((ua ^ ub) >> top) == 0;
+}
+
 // min(num/den, 1) for num, den nonzero with the same sign.  When
 // |num| >= |den| the quotient rounds to >= 1, so the division is skipped.
 template <typename R>
 __device__ __forceinline__ R limited_ratio(R num, R den)
 {
-    return (Fp<R>::abs(num) >= Fp<R>::abs(den)) ? R(1) : Fp<R>::div(num, den);
-}
-
-template <typename R>
-__device__ __forceinline__ bool same_sign(R a, R b)
-{
-    return (a > R(0) && b > R(0)) || (a < R(0) && b < R(0));
+    const auto mag = ~(decltype(fbits(num)))0 >> 1;
+    return (fbits(num) & mag) >= (fbits(den) & mag) ? R(1) : Fp<R>::div(num, den);
 }
 
 // Limited states at the interface between cells a (left) and b (right)

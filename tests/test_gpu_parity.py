@@ -219,6 +219,20 @@ def test_register_variant_rejects_unsupported():
         assert e.value.status == S.EINVAL
 
 
+@pytest.mark.parametrize("eq", ["heat", "ks"])
+def test_large_size_swept_equals_classic(eq):
+    """At N = 2^24 (FP32 arrays of 64 MB, the bandwidth regime of the classic
+    kernel) the swept and classic paths still agree bit for bit."""
+    N = 1 << 24
+    spec = spec_for(eq, "periodic", N)
+    u0 = I.initial_state(spec, np.float32)
+    steps = 600 if eq == "heat" else 150
+    a = _gpu(spec, u0, steps, "f32", "classic")
+    b = _gpu(spec, u0, steps, "f32", "swept", 4096 if eq == "heat" else 1024)
+    assert np.array_equal(a, b)
+    assert np.all(np.isfinite(a))
+
+
 def test_invalid_node_width_rejected():
     spec = spec_for("ks", "periodic", 1000)
     with S.Problem(spec, state_for(spec)) as p:
