@@ -22,7 +22,7 @@ def lib():
 def _declared():
     text = open(os.path.join(ROOT, "include", "swept.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(swp_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(swp_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_binding_symbols():
