@@ -339,6 +339,25 @@ def run_served(count: int, lam: float, seed: int, budget: int, baseline: bool = 
     return res
 
 
+def other_configs() -> dict:
+    """The heat configuration (N = 1024, r = 0.25, 4096 steps, 64 points per
+    node) and the Sod tube at N = 2^20 (4096 steps, dt/dx = 0.2): swept against
+    classic, FP64, device-timed."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    out = {}
+    for name, eq, N, steps, n in (("heat N=1024 r=0.25 4096 steps n=64", "heat", 1024, 4096, 64),
+                                  ("Sod Euler N=2^20 4096 steps", "euler", 1 << 20, 4096, 256)):
+        spec, u0 = _spec_ic(eq, N)
+        u0d = torch.from_numpy(u0).cuda()
+        with S.Problem(spec, u0d) as p:
+            ts = _time_solve(p, u0d, steps, "swept", n, "graph" if eq == "heat" else "per_phase")
+            tc = _time_solve(p, u0d, steps, "classic", launch="graph")
+        out[name] = {"swept": N * steps / ts / 1e9, "classic_graph": N * steps / tc / 1e9,
+                     "unit": UNIT, "swept_speedup": tc / ts}
+    return out
+
+
 def fp32_error() -> dict:
     """FP32 heat / KS against the FP64 oracle (reported, not gated)."""
     import oracle as O
@@ -507,6 +526,7 @@ def run_gpu(args, wl):
         }
         line["batched"] = run_batched()
         line["fp32_rel_error_vs_fp64_oracle"] = fp32_error()
+        line["other_configs"] = other_configs()
     print(json.dumps(line), flush=True)
     dist.close()
 

@@ -166,7 +166,8 @@ size_t swp_memory_in_use(void);
  * pays a launch per phase each.  A batch advances every problem given to it
  * in one persistent launch per precision (heat and KS together, Euler in a
  * launch of its own): work is a table of
- * (problem, phase) tasks in phase-major order; each block claims one node of
+ * (problem, phase) tasks ordered by estimated start time (each problem's
+ * phases in order); each block claims one node of
  * the current task at a time and waits, bounded, for the problem's two
  * neighbouring nodes of the previous phase (the paper's kernel-boundary
  * synchronisation of Section 3, done per node instead of per grid).  Each

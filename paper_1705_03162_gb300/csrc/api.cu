@@ -156,6 +156,7 @@ swp_status check_width(const swp_problem* p, int n)
     const int step = 4 * p->rad;
     if (n < step || n % step) return fail(SWP_EINVAL, "points_per_block %d must be a positive multiple of %d", n, step);
     if (p->N % n) return fail(SWP_EINVAL, "points_per_block %d must divide n_points %lld", n, (long long)p->N);
+    if (p->N / n > 0x7FFFFFFF) return fail(SWP_EINVAL, "points_per_block %d gives more than 2^31 - 1 nodes", n);
     if (swept_smem_bytes(p->desc.eq, n, p->esize) > max_smem(p->device))
         return fail(SWP_EINVAL, "points_per_block %d needs %zu bytes of shared memory (max %zu)", n,
                     swept_smem_bytes(p->desc.eq, n, p->esize), max_smem(p->device));
@@ -753,11 +754,29 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         max_phases = std::max(max_phases, it.s.n_phases);
         smem = std::max(smem, swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
     }
-    // (instance, phase) tasks, phase-major
-    std::vector<int2> tasks;
-    for (int64_t ph = 0; ph < max_phases; ++ph)
-        for (size_t i = 0; i < items.size(); ++i)
-            if (items[i].s.n_phases > ph) tasks.push_back(make_int2((int)i, (int)ph));
+    // (instance, phase) tasks in order of estimated start: phase p of instance
+    // i at p * c_i, with c_i the cost of one of its phase items (levels times
+    // FP64 operations per point, times the warp rows of its widest level).
+    // Each instance keeps its phases in order, so every item depends only on
+    // items of earlier tasks; instances with short items run ahead instead of
+    // waiting, phase by phase, for instances with long ones.
+    struct Key {
+        double start;
+        int inst, phase;
+    };
+    std::vector<Key> keys;
+    for (size_t i = 0; i < items.size(); ++i) {
+        const auto& s = items[i].s;
+        const double ops = items[i].p->desc.eq == SWP_HEAT ? 3.0 : (items[i].p->desc.eq == SWP_KS ? 7.0 : 260.0);
+        const double rows = std::max(1.0, (double)s.n / 256.0);
+        const double cost = (2.0 * s.H - 1.0) * ops * rows;
+        for (int64_t ph = 0; ph < s.n_phases; ++ph) keys.push_back(Key{(double)ph * cost, (int)i, (int)ph});
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
+        return x.start < y.start || (x.start == y.start && x.phase < y.phase);
+    });
+    std::vector<int2> tasks(keys.size());
+    for (size_t t = 0; t < keys.size(); ++t) tasks[t] = make_int2(keys[t].inst, keys[t].phase);
     if (tasks.size() >= (size_t)1 << 30 || flags >= (int64_t)1 << 30)
         return fail(SWP_EINVAL, "batch too large for one launch");
     swp_status st;

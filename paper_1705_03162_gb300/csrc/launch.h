@@ -69,7 +69,7 @@ int swept_persistent_blocks_per_sm(int eq, int n, int threads);
 // ---------------------------------------------------------------------------
 // Batched swept advance: many independent problems of one precision in one
 // persistent launch (heat and KS together; Euler in its own launch).  Work is a table of (instance, phase)
-// tasks in phase-major order; a block claims one node of the current task at
+// tasks, each instance's phases in order; a block claims one node of the current task at
 // a time, so items are claimed in dependency order, and waits (bounded) for
 // the instance's two neighbouring nodes of the previous phase.
 // ---------------------------------------------------------------------------
@@ -85,7 +85,7 @@ template <typename R> struct BatchInst {
 };
 
 struct BatchWork {
-    const int2* tasks;    // (instance, phase), phase-major
+    const int2* tasks;    // (instance, phase), each instance's phases in order
     int* task_ctr;        // nodes claimed per task (zeroed per launch)
     int* cur_task;        // first task with unclaimed nodes (zeroed per launch)
     int ntasks;
