@@ -347,7 +347,7 @@ def other_configs() -> dict:
     from paper_1705_03162_gb300 import swept as S
     out = {}
     for name, eq, N, steps, n in (("heat N=1024 r=0.25 4096 steps n=64", "heat", 1024, 4096, 64),
-                                  ("Sod Euler N=2^20 4096 steps", "euler", 1 << 20, 4096, 256)):
+                                  ("Sod Euler N=2^20 4096 steps n=512", "euler", 1 << 20, 4096, 512)):
         spec, u0 = _spec_ic(eq, N)
         u0d = torch.from_numpy(u0).cuda()
         with S.Problem(spec, u0d) as p:
@@ -577,6 +577,33 @@ def run_sweep(steps: int = 2000):
                               "register": reg, "swept_speedup": best / classic}), flush=True)
 
 
+def run_sod(exps, steps: int, widths=None, threads=None):
+    """Sod shock tube (dt/dx = 0.2, Dirichlet ends), FP64, fixed step count:
+    swept at each node width and block size against classic on a stream and as
+    a CUDA graph; one JSON line per N."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    for e in exps:
+        N = 1 << e
+        spec, u0 = _spec_ic("euler", N)
+        u0d = torch.from_numpy(u0).cuda()
+        with S.Problem(spec, u0d) as p:
+            classic = N * steps / _time_solve(p, u0d, steps, "classic") / 1e9
+            classic_graph = N * steps / _time_solve(p, u0d, steps, "classic", launch="graph") / 1e9
+            runs = []
+            for n in widths or (64, 128, 256, 512):
+                if N % n or N // n < 2:
+                    continue
+                for t in threads or (128, 256):
+                    r = N * steps / _time_solve(p, u0d, steps, "swept", n, "per_phase", t) / 1e9
+                    runs.append({"points_per_block": n, "threads": t, "swept": r})
+        best = max(runs, key=lambda x: x["swept"])
+        print(json.dumps({"sod": f"N=2^{e}", "timesteps": steps, "dtype": "f64", "unit": UNIT,
+                          "classic": classic, "classic_graph": classic_graph, "swept_best": best,
+                          "swept_speedup_vs_graph": best["swept"] / classic_graph, "swept_runs": runs}),
+              flush=True)
+
+
 def run_bandwidth(steps: int = 200):
     """Classic FP32 heat and KS at N = 2^26 (arrays far beyond L2): achieved
     algorithmic HBM bandwidth against the measured copy peak."""
@@ -607,22 +634,35 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--points-per-block", type=int, default=DEFAULT_WORKLOAD["points_per_block"])
+    ap.add_argument("--points-per-block", type=int, default=None)
     ap.add_argument("--launch", choices=["per_phase", "persistent", "auto"], default=DEFAULT_WORKLOAD["launch"])
-    ap.add_argument("--threads", type=int, default=DEFAULT_WORKLOAD["threads"])
-    ap.add_argument("--timesteps", type=int, default=DEFAULT_WORKLOAD["steps"])
+    ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--timesteps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the per-size sweep lines instead")
     ap.add_argument("--bandwidth", action="store_true", help="print the classic FP32 bandwidth lines instead")
+    ap.add_argument("--sod", type=int, nargs="*", metavar="LOG2N",
+                    help="print Sod swept-vs-classic lines for N = 2^LOG2N (default 11 14 17 20) instead; "
+                         "--timesteps defaults to 4096 here, and --points-per-block / --threads, when given, "
+                         "fix the swept configuration")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the served, batched and FP32-error measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = dict(DEFAULT_WORKLOAD, points_per_block=args.points_per_block, launch=args.launch,
-              threads=args.threads, steps=args.timesteps)
+    wl = dict(DEFAULT_WORKLOAD, launch=args.launch)
+    for key, val in (("points_per_block", args.points_per_block), ("threads", args.threads),
+                     ("steps", args.timesteps)):
+        if val is not None:
+            wl[key] = val
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.sod is not None:
+        from paper_1705_03162_gb300 import swept as S
+        S.load_library()
+        run_sod(args.sod or [11, 14, 17, 20], args.timesteps or 4096,
+                [args.points_per_block] if args.points_per_block else None,
+                [args.threads] if args.threads else None)
     elif args.sweep or args.bandwidth:
         from paper_1705_03162_gb300 import swept as S
         S.load_library()

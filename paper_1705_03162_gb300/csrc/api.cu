@@ -164,15 +164,16 @@ swp_status check_width(const swp_problem* p, int n)
 }
 
 // Default node width, from the widths measured fastest on GB300 for single
-// problems: about N / 1024 points, at least 64 (heat) or 128 (KS, Euler) and
-// at most 1024 (Euler 512); the nearest width that divides N, is a multiple
-// of 4 rad and fits shared memory.
+// problems: about N / 1024 points for heat and KS (at least 64 and 128, at
+// most 1024) and N / 256 for Euler (64 to 512); the nearest width that
+// divides N, is a multiple of 4 rad and fits shared memory.
 int default_width(const swp_problem* p)
 {
     const int step = 4 * p->rad;
-    const int lo = p->desc.eq == SWP_HEAT ? 64 : 128;
-    const int cap = p->desc.eq == SWP_EULER ? 512 : 1024;
-    int64_t target = p->N / 1024;
+    const bool euler = p->desc.eq == SWP_EULER;
+    const int lo = (p->desc.eq == SWP_HEAT || euler) ? 64 : 128;
+    const int cap = euler ? 512 : 1024;
+    int64_t target = p->N / (euler ? 256 : 1024);
     if (target < lo) target = lo;
     if (target > cap) target = cap;
     if (target > p->N / 2) target = p->N / 2;

@@ -116,7 +116,7 @@ __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R*
 
 // Advance levels j_lo..j_hi of one node in shared memory.
 //   row0 / row1 : [NV][W] even / odd level rows
-//   P, G        : Euler scratch, W pressures and [3][W + 1] interface values
+//   P, G        : Euler scratch, W pressures, [3][W + 1] + 3 interface values, 8 ghost values
 //   wall        : the node may evaluate points next to a non-periodic end
 template <typename R, int EQ>
 __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n, int H, int j_lo,
@@ -157,54 +157,74 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
             }
         } else {
             const R kh = c.kh[stage];
+            // pressures of cells [lo-2, hi+2), interfaces [lo, hi], then cells
+            const int GW = W + 1;
+            R* Gx = G + 3 * GW;   // wall nodes: the interface between cell N-1 and the right ghost
+            // ghost states, variable v of the left / right end at Gh[2v] /
+            // Gh[2v + 1], and their pressures at Gh[6] / Gh[7]
+            R* Gh = Gx + 3;
+            // Slots wrap modulo N; next to a Dirichlet end s0 is the slot of
+            // cell 0 (W when the window does not wrap), so slots below s0 hold
+            // cells ..., N-2, N-1.  Periodic ends: no slot is special.
+            int s0 = INT_MIN / 2;
             if (wall) {
-                // each cell gathers its five neighbours through the boundary
-                for (int t = threadIdx.x; t < cnt; t += T) {
-                    const int q = lo + t;
-                    R qs[5][3], p[5];
+                const int64_t w0 = wrap(-g0, N);
+                s0 = w0 < W ? (int)w0 : W;
+            }
+            if (wall && threadIdx.x < 2) {
+                const R* gs = threadIdx.x ? c.ghost_r : c.ghost_l;
+                Gh[threadIdx.x] = gs[0];
+                Gh[2 + threadIdx.x] = gs[1];
+                Gh[4 + threadIdx.x] = gs[2];
+                Gh[6 + threadIdx.x] = euler_pressure(gs[0], gs[1], gs[2], c.gm1);
+            }
+            for (int t = threadIdx.x; t < cnt + 4; t += T) {
+                const int s = lo - 2 + t;
+                P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1);
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t <= cnt; t += T) {
+                const int sb = lo + t;   // interface between slots sb-1 and sb
+                // Where cell 0 sits at slot sb == s0, the slot boundary stands
+                // for two interfaces: -1 | 0 (in G) and N-1 | N (in Gx).
+                const int reps = sb == s0 ? 2 : 1;
+                for (int rep = 0; rep < reps; ++rep) {
+                    // interface among cells 0, 1, ... (slots >= s0) or among
+                    // ..., N-2, N-1 (slots < s0); a stencil cell on the other
+                    // side of s0 is the ghost state of that end
+                    const bool left_end = rep == 0 && sb >= s0;
+                    R q[2][3], p[4];
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) {
+                    for (int d = 0; d < 4; ++d) {
+                        const int s = sb + d - 2;
+                        const bool lg = left_end && s < s0, rg = !left_end && s >= s0;
+                        const bool gh = lg || rg;
+                        const R* cell = gh ? Gh + (rg ? 1 : 0) : src + s;
+                        const int vs = gh ? 2 : W;
+                        p[d] = gh ? Gh[6 + (rg ? 1 : 0)] : P[s];
+                        if (d == 1 || d == 2) {
 #pragma unroll
-                        for (int v = 0; v < 3; ++v)
-                            qs[k][v] = wall_fetch(src, W, q, k - 2, v, g0, N, bc, c);
-                        p[k] = euler_pressure(qs[k][0], qs[k][1], qs[k][2], c.gm1);
+                            for (int v = 0; v < 3; ++v) q[d - 1][v] = cell[v * vs];
+                        }
                     }
-                    R gm[3], gp[3];
-                    euler_interface(qs[1], qs[2], p[0], p[1], p[2], p[3], c.gm1, c.ggm1, gm);
-                    euler_interface(qs[2], qs[3], p[1], p[2], p[3], p[4], c.gm1, c.ggm1, gp);
-#pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        const R base = stage == 0 ? src[v * W + q] : row0[v * W + q];
-                        dst[v * W + q] = euler_update(gp[v], gm[v], base, kh);
-                    }
-                }
-            } else {
-                // pressures of cells [lo-2, hi+2), interfaces [lo, hi], then cells
-                const int GW = W + 1;
-                for (int t = threadIdx.x; t < cnt + 4; t += T) {
-                    const int s = lo - 2 + t;
-                    P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1);
-                }
-                __syncthreads();
-                for (int t = threadIdx.x; t <= cnt; t += T) {
-                    const int sb = lo + t;   // interface between slots sb-1 and sb
-                    R qa[3] = {src[sb - 1], src[W + sb - 1], src[2 * W + sb - 1]};
-                    R qb[3] = {src[sb], src[W + sb], src[2 * W + sb]};
                     R g3[3];
-                    euler_interface(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], c.gm1, c.ggm1,
-                                    g3);
-                    G[sb] = g3[0];
-                    G[GW + sb] = g3[1];
-                    G[2 * GW + sb] = g3[2];
+                    euler_interface(q[0], q[1], p[0], p[1], p[2], p[3], c.gm1, c.ggm1, g3);
+                    R* o = rep ? Gx : G + sb;
+                    const int os = rep ? 1 : GW;
+                    o[0] = g3[0];
+                    o[os] = g3[1];
+                    o[2 * os] = g3[2];
                 }
-                __syncthreads();
-                for (int t = threadIdx.x; t < cnt; t += T) {
-                    const int q = lo + t;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < cnt; t += T) {
+                const int q = lo + t;
+                const bool last = q == s0 - 1;   // cell N-1: right interface in Gx
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        const R base = stage == 0 ? src[v * W + q] : row0[v * W + q];
-                        dst[v * W + q] = euler_update(G[v * GW + q + 1], G[v * GW + q], base, kh);
-                    }
+                for (int v = 0; v < 3; ++v) {
+                    const R base = stage == 0 ? src[v * W + q] : row0[v * W + q];
+                    const R gp = last ? Gx[v] : G[v * GW + q + 1];
+                    dst[v * W + q] = euler_update(gp, G[v * GW + q], base, kh);
                 }
             }
         }
@@ -218,7 +238,7 @@ __host__ __device__ __forceinline__ size_t smem_elems(int n)
     constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
     const size_t W = (size_t)window_width(n, RAD);
     size_t e = 2 * NV * W;
-    if (EQ == EULER) e += W + 3 * (W + 1);
+    if (EQ == EULER) e += W + 3 * (W + 1) + 11;
     return e;
 }
 
