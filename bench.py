@@ -216,7 +216,8 @@ def _spec_ic(eq: str, N: int, dtype=np.float64):
 
 def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
     """4096 independent heat + KS instances, N log-uniform 2^10..2^16, steps
-    U(10^3, 10^4), one persistent launch per precision, autotuned node widths;
+    U(10^3, 10^4), one persistent launch per precision, scheme (swept or
+    classic) and width autotuned per (equation, power-of-two N) bucket;
     against advancing a sample of the same instances one by one."""
     import math
     import torch
@@ -234,26 +235,30 @@ def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
         for eq in ("heat", "ks"):
             for e in range(10, 17):
                 spec, u0 = _spec_ic(eq, 2 ** e, npdt)
-                tuned[(eq, e)] = S.autotune_width(spec, u0, count=32, steps=256, dtype=dtype)
+                tuned[(eq, e)] = S.autotune(spec, u0, count=32, steps=256, dtype=dtype)
         tune_s = time.perf_counter() - t0
         stream = torch.cuda.Stream()
-        probs, widths = [], []
+        probs, schemes, widths = [], [], []
         for eq, N, steps in cases:
             spec, u0 = _spec_ic(eq, N, npdt)
             probs.append(S.Problem(spec, u0, dtype, stream=stream))
-            n = tuned[(eq, min(max(int(round(math.log2(N))), 10), 16))]
-            while N % n:
-                n //= 2
+            scheme, n = tuned[(eq, min(max(int(round(math.log2(N))), 10), 16))]
+            if scheme == "swept":
+                while N % n:
+                    n //= 2
+            else:
+                n = min(n, N)
+            schemes.append(scheme)
             widths.append(n)
         steps = [c[2] for c in cases]
         upd = float(sum(c[1] * c[2] for c in cases))
         with S.Batch(stream) as bt:
-            bt.advance(probs, [min(s, 64) for s in steps], widths)   # warm-up
+            bt.advance_ex(probs, [min(s, 64) for s in steps], schemes, widths)   # warm-up
             bt.synchronize()
             l0 = bt.kernel_launches()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            bt.advance(probs, steps, widths)
+            bt.advance_ex(probs, steps, schemes, widths)
             ev1.record(stream)
             bt.synchronize()
             ms = ev0.elapsed_time(ev1)
@@ -263,14 +268,14 @@ def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in sample:
-            probs[i].advance(steps[i], "swept", widths[i])
+            probs[i].advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
         torch.cuda.synchronize()
         per_inst = su / (time.perf_counter() - t0) / 1e9
         for p in probs:
             p.close()
         out[dtype] = {"value": upd / ms / 1e6, "unit": UNIT, "ms": ms, "kernel_launches": launches,
-                      "per_instance_swept_value": per_inst, "autotune_s": tune_s,
-                      "tuned_widths": {f"{k[0]}2^{k[1]}": v for k, v in tuned.items()}}
+                      "per_instance_value": per_inst, "autotune_s": tune_s,
+                      "tuned": {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}}
     return out
 
 

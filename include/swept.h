@@ -61,7 +61,10 @@ typedef enum { SWP_BC_PERIODIC = 0, SWP_BC_REFLECTIVE = 1, SWP_BC_DIRICHLET = 2 
 
 typedef enum { SWP_F64 = 0, SWP_F32 = 1 } swp_dtype;   /* Euler: SWP_F64 only */
 
-typedef enum { SWP_CLASSIC = 0, SWP_SWEPT = 1 } swp_scheme;
+/* SWP_SCHEME_AUTO: the scheme (and width) swp_autotune measured faster for
+ * the problem's (equation, dtype, n_points); swept at the tuned or default
+ * width when none was measured. */
+typedef enum { SWP_CLASSIC = 0, SWP_SWEPT = 1, SWP_SCHEME_AUTO = 2 } swp_scheme;
 
 /* Problem description.
  *   n_points : N grid points (cells for Euler), N >= 5
@@ -161,18 +164,22 @@ swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes);
 swp_status swp_set_memory_budget(size_t bytes);
 size_t swp_memory_in_use(void);
 
-/* ---- Batched swept advance (many independent problems, one launch) ----
+/* ---- Batched advance (many independent problems, one launch) ----
  * Advancing many small problems one by one leaves most of the GPU idle and
  * pays a launch per phase each.  A batch advances every problem given to it
  * in one persistent launch per precision (heat and KS together, Euler in a
- * launch of its own): work is a table of
- * (problem, phase) tasks ordered by estimated start time (each problem's
- * phases in order); each block claims one node of
- * the current task at a time and waits, bounded, for the problem's two
- * neighbouring nodes of the previous phase (the paper's kernel-boundary
- * synchronisation of Section 3, done per node instead of per grid).  Each
- * problem's result is bit-identical to swp_advance with the same node width.
- * The paper has no batched form. */
+ * launch of its own): work is a table of (problem, phase) tasks ordered by
+ * estimated start time (each problem's phases in order); each block claims
+ * one item of the current task at a time and waits, bounded, for the items
+ * of the problem's previous phase that it reads (the paper's kernel-boundary
+ * synchronisation of Section 3, done per item instead of per grid).
+ *   swept problem   : a phase is a triangle / diamond, an item one node;
+ *   classic problem : a phase is one sub-timestep (Section 5.1), an item one
+ *                     chunk of the balanced partition of [0, N) into
+ *                     ceil(N / m) chunks of at most m points.
+ * Each problem's result is bit-identical to swp_advance with the same scheme
+ * (and, swept, the same node width).  The table costs 12 bytes of device
+ * memory per (problem, phase) task.  The paper has no batched form. */
 typedef struct swp_batch swp_batch;
 
 /* A batch runs its work on cuda_stream (NULL = legacy default stream); every
@@ -186,6 +193,24 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out);
  * SWP_ETIMEOUT surfaces at swp_batch_synchronize. */
 swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
                              int32_t count, const int32_t* points_per_block, int32_t threads);
+
+/* Like swp_batch_advance, with a scheme per problem and a launch form.
+ *   schemes          : SWP_SWEPT, SWP_CLASSIC or SWP_SCHEME_AUTO per problem
+ *                      (NULL = all SWP_SCHEME_AUTO)
+ *   points_per_block : swept node width / classic chunk width m (4 <= m <= N)
+ *                      per problem; NULL or 0 = the tuned width, else the
+ *                      default (classic: min(N, 1024), Euler min(N, 256))
+ *   launch           : SWP_LAUNCH_AUTO or _PERSISTENT (upload the task table
+ *                      and launch), or SWP_LAUNCH_GRAPH: the launch is
+ *                      captured as a CUDA graph with tables of its own on the
+ *                      first advance of these problems, in their current
+ *                      rows, with these plans, and replayed when the same
+ *                      advance comes again (at most 8 graphs per batch, the
+ *                      oldest dropped first).
+ * Errors as swp_batch_advance; SWP_ENOMEM when the tables do not fit. */
+swp_status swp_batch_advance_ex(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
+                                int32_t count, const int32_t* schemes, const int32_t* points_per_block,
+                                int32_t threads, int32_t launch);
 swp_status swp_batch_synchronize(swp_batch* b);
 swp_status swp_batch_destroy(swp_batch* b);
 int64_t swp_batch_kernel_launches(const swp_batch* b);
@@ -198,8 +223,20 @@ int64_t swp_batch_kernel_launches(const swp_batch* b);
  * trial problems; synchronises the device. */
 swp_status swp_autotune_width(const swp_desc* desc, const void* u0_host, int32_t batch_count,
                               int64_t steps, int32_t* best_n);
-/* The tuned width for desc's (equation, dtype, n_points), or 0 if none. */
+/* The tuned swept width for desc's (equation, dtype, n_points), or 0 if none. */
 swp_status swp_tuned_width(const swp_desc* desc, int32_t* n);
+
+/* Scheme autotuner.  Times the swept widths as swp_autotune_width does and
+ * the classic scheme in the same batched form (chunks of 256, 1024 and 4096
+ * points, capped at N), keeps whichever is faster for desc's (equation,
+ * dtype, n_points) and returns it: best_scheme SWP_SWEPT or SWP_CLASSIC,
+ * best_n its node or chunk width.  SWP_SCHEME_AUTO advances (single or
+ * batched) of problems with that key then use it.  Allocates and frees its
+ * own trial problems; synchronises the device. */
+swp_status swp_autotune(const swp_desc* desc, const void* u0_host, int32_t batch_count, int64_t steps,
+                        int32_t* best_scheme, int32_t* best_n);
+/* The tuned choice for desc's key: scheme and width (SWP_SWEPT, 0 if none). */
+swp_status swp_tuned(const swp_desc* desc, int32_t* scheme, int32_t* n);
 
 /* ---- Serving with continuous batching ----
  * A server owns a scheduler thread that admits solve requests as they arrive

@@ -184,6 +184,53 @@ int default_width(const swp_problem* p)
     return 0;
 }
 
+// Choices measured by the autotuners, per (equation, dtype, n_points).
+struct Tuned {
+    int scheme = SWP_SWEPT;   // the faster scheme (swp_autotune)
+    int n = 0;                // its width: swept node or classic chunk
+    int n_swept = 0;          // the fastest swept node width
+};
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int64_t>, Tuned> g_tuned;
+
+bool tuned_of(const swp_desc& d, Tuned* t)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tuned.find(std::make_tuple(d.eq, d.dtype, d.n_points));
+    if (it == g_tuned.end()) return false;
+    *t = it->second;
+    return true;
+}
+
+// Swept node width for a problem: the tuned one if measured, else the
+// default rule.
+int width_for(const swp_problem* p)
+{
+    Tuned t;
+    if (tuned_of(p->desc, &t) && t.n_swept > 0 && check_width(p, t.n_swept) == SWP_OK) return t.n_swept;
+    return default_width(p);
+}
+
+// Classic chunk width of a batched classic advance (points per item).
+int default_chunk(const swp_problem* p)
+{
+    return (int)std::min<int64_t>(p->N, p->desc.eq == SWP_EULER ? 256 : 1024);
+}
+
+// SWP_SCHEME_AUTO: the scheme swp_autotune measured faster (with its width),
+// else swept at width_for.
+void choice_for(const swp_problem* p, int* scheme, int* n)
+{
+    Tuned t;
+    if (tuned_of(p->desc, &t) && t.scheme == SWP_CLASSIC && t.n > 0) {
+        *scheme = SWP_CLASSIC;
+        *n = t.n;
+        return;
+    }
+    *scheme = SWP_SWEPT;
+    *n = width_for(p);
+}
+
 template <typename R>
 const Coefs<R>& coefs_of(const swp_problem* p);
 template <>
@@ -426,8 +473,14 @@ swp_status run_graph(swp_problem* p, int64_t steps, int scheme, int n, int threa
 }
 
 template <typename R>
-swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& o)
+swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& o_in)
 {
+    swp_advance_opts o = o_in;
+    if (o.scheme == SWP_SCHEME_AUTO) {
+        int n = 0;
+        choice_for(p, &o.scheme, &n);
+        if (o.scheme == SWP_SWEPT && o.points_per_block == 0) o.points_per_block = n;
+    }
     if (o.scheme == SWP_CLASSIC) {
         if (o.launch == SWP_LAUNCH_GRAPH) {
             const int thr = o.threads <= 0 ? 256 : o.threads;
@@ -582,7 +635,7 @@ swp_status swp_advance_ex(swp_problem* p, int64_t n_steps, const swp_advance_opt
 {
     if (!p || !opts) return fail(SWP_EINVAL, "problem or opts is NULL");
     if (n_steps < 0) return fail(SWP_EINVAL, "n_steps must be >= 0");
-    if (opts->scheme != SWP_CLASSIC && opts->scheme != SWP_SWEPT)
+    if (opts->scheme != SWP_CLASSIC && opts->scheme != SWP_SWEPT && opts->scheme != SWP_SCHEME_AUTO)
         return fail(SWP_EINVAL, "unknown scheme %d", opts->scheme);
     if (n_steps == 0) return SWP_OK;
     if (n_steps > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps too large");
@@ -680,24 +733,55 @@ const char* swp_last_error(void) { return g_last_error.c_str(); }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Batched swept advance and node-width autotuner.
+// Batched advance (swept and classic instances in one persistent launch) and
+// the autotuners.
 // ---------------------------------------------------------------------------
+namespace {
+
+// Device tables of one persistent batch launch.
+struct BatchTables {
+    void* insts = nullptr;     size_t insts_cap = 0;
+    int2* tasks = nullptr;     size_t tasks_cap = 0;
+    int* ctr = nullptr;        size_t ctr_cap = 0;     // [0] = cur_task, [1..] = task counters
+    uint32_t* flags = nullptr; size_t flags_cap = 0;
+    void release()
+    {
+        if (insts) cudaFree(insts);
+        if (tasks) cudaFree(tasks);
+        if (ctr) cudaFree(ctr);
+        if (flags) cudaFree(flags);
+        *this = BatchTables();
+    }
+};
+
+// A batch launch captured as a CUDA graph (zero the counters and flags, run
+// the persistent kernel), with tables of its own; replayed when the same
+// problems, in the same rows, advance by the same plans again.
+struct BatchGraph {
+    std::vector<int64_t> key;
+    BatchTables t;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<swp_problem*> flip;   // problems whose state ends in the other row
+    std::vector<swp_problem*> all;
+};
+
+}  // namespace
+
 struct swp_batch {
     cudaStream_t stream = nullptr;
     int device = 0, sms = 0;
     int64_t launches = 0;
-    // device workspace, grown on demand
-    void* insts = nullptr;   size_t insts_cap = 0;
-    int2* tasks = nullptr;   size_t tasks_cap = 0;
-    int* ctr = nullptr;      size_t ctr_cap = 0;     // [0] = cur_task, [1] = status, [2..] = task counters
-    uint32_t* flags = nullptr; size_t flags_cap = 0;
+    BatchTables t;                     // plain launches, grown on demand
+    int* status = nullptr;             // != 0: a bounded wait gave up (sticky until synchronize)
+    void* stage = nullptr;             // pinned staging of the table uploads
+    size_t stage_cap = 0;
+    cudaEvent_t staged = nullptr;      // the last upload out of `stage` has finished
+    std::vector<BatchGraph> graphs;    // at most 8, oldest first
+    cudaStream_t capture_stream = nullptr;
     uint64_t wait_limit_ns = 2000000000ull;
 };
 
 namespace {
-
-std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int64_t>, int> g_tuned;   // (eq, dtype, N) -> node width
 
 swp_status grow(void** p, size_t* cap, size_t bytes)
 {
@@ -712,28 +796,73 @@ swp_status grow(void** p, size_t* cap, size_t bytes)
     return SWP_OK;
 }
 
-// Node width for a problem: the tuned value for (eq, dtype, N) if the tuner
-// measured one, else the default rule.
-int width_for(const swp_problem* p)
+swp_status grow_tables(BatchTables& t, size_t inst_bytes, size_t ntasks, size_t nflags)
 {
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tuned.find(std::make_tuple(p->desc.eq, p->desc.dtype, p->N));
-        if (it != g_tuned.end() && check_width(p, it->second) == SWP_OK) return it->second;
-    }
-    return default_width(p);
+    swp_status st;
+    if ((st = grow(&t.insts, &t.insts_cap, inst_bytes)) != SWP_OK) return st;
+    if ((st = grow((void**)&t.tasks, &t.tasks_cap, sizeof(int2) * ntasks)) != SWP_OK) return st;
+    if ((st = grow((void**)&t.ctr, &t.ctr_cap, sizeof(int) * (ntasks + 1))) != SWP_OK) return st;
+    return grow((void**)&t.flags, &t.flags_cap, sizeof(uint32_t) * nflags);
 }
 
 struct BatchItem {
     swp_problem* p;
-    SweptPlan s;
+    int kind;       // BATCH_SWEPT / BATCH_CLASSIC
+    SweptPlan s;    // swept plan; classic: n = widest chunk, K = chunks, n_phases = sub-steps
+    bool flip;      // the state ends in the other row
 };
 
-template <typename R>
-swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads)
+// Classic instance of a batch: K = ceil(N / m) chunks of the balanced
+// partition (each at least N / K >= m / 2 >= rad points, so a point's stencil
+// stays within its chunk's two neighbours), one phase per sub-timestep.
+SweptPlan plan_classic(const swp_problem* p, int64_t steps, int m)
 {
+    SweptPlan s{};
+    s.K = (int)((p->N + m - 1) / m);
+    s.n = (int)((p->N + s.K - 1) / s.K);
+    s.T = steps * p->sub;
+    s.n_phases = s.T;
+    return s;
+}
+
+swp_status check_chunk(const swp_problem* p, int m)
+{
+    if (m < 4 || m > p->N) return fail(SWP_EINVAL, "classic chunk width %d must be in [4, n_points]", m);
+    if (batch_classic_smem_bytes(p->desc.eq, m, p->esize) > max_smem(p->device))
+        return fail(SWP_EINVAL, "classic chunk width %d does not fit shared memory", m);
+    return SWP_OK;
+}
+
+// Estimated FP64-pipe operations per point of one level (sub-timestep).
+double level_cost(int eq) { return eq == SWP_HEAT ? 3.0 : (eq == SWP_KS ? 7.0 : 100.0); }
+
+template <typename R>
+swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads, bool graph)
+{
+    std::vector<int64_t> key;
+    if (graph) {
+        key.reserve(items.size() * 5 + 2);
+        key.push_back(mode);
+        key.push_back(threads);
+        for (const auto& it : items) {
+            key.push_back((int64_t)(intptr_t)it.p);
+            key.push_back(it.p->cur);
+            key.push_back(it.kind);
+            key.push_back(it.s.n);
+            key.push_back(it.s.T);
+        }
+        for (auto& g : b->graphs)
+            if (g.key == key) {
+                cudaError_t e = cudaGraphLaunch(g.exec, b->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+                b->launches++;
+                for (auto* p : g.all) p->launches++;
+                for (auto* p : g.flip) p->cur = 1 - p->cur;
+                return SWP_OK;
+            }
+    }
     std::vector<BatchInst<R>> insts(items.size());
-    int64_t flags = 0, max_phases = 0;
+    int64_t flags = 0, items_total = 0;
     size_t smem = 0;
     for (size_t i = 0; i < items.size(); ++i) {
         const BatchItem& it = items[i];
@@ -750,80 +879,216 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         in.n_phases = it.s.n_phases;
         in.flag_off = (int)flags;
         in.eq = it.p->desc.eq;
+        in.kind = it.kind;
         in.c = coefs_of<R>(it.p);
         flags += it.s.K;
-        max_phases = std::max(max_phases, it.s.n_phases);
-        smem = std::max(smem, swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
+        items_total += it.s.n_phases * it.s.K;
+        smem = std::max(smem, it.kind == BATCH_SWEPT ? swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize)
+                                                     : batch_classic_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
     }
     // (instance, phase) tasks in order of estimated start: phase p of instance
-    // i at p * c_i, with c_i the cost of one of its phase items (levels times
-    // FP64 operations per point, times the warp rows of its widest level).
-    // Each instance keeps its phases in order, so every item depends only on
-    // items of earlier tasks; instances with short items run ahead instead of
+    // i at p * c_i, with c_i the cost of one of its items (levels times FP64
+    // operations per point, times the warp rows of its widest level).  Each
+    // instance keeps its phases in order, so every item depends only on items
+    // of earlier tasks; instances with short items run ahead instead of
     // waiting, phase by phase, for instances with long ones.
     struct Key {
         double start;
         int inst, phase;
     };
     std::vector<Key> keys;
+    keys.reserve((size_t)std::min<int64_t>(items_total, (int64_t)1 << 30));
     for (size_t i = 0; i < items.size(); ++i) {
         const auto& s = items[i].s;
-        const double ops = items[i].p->desc.eq == SWP_HEAT ? 3.0 : (items[i].p->desc.eq == SWP_KS ? 7.0 : 260.0);
         const double rows = std::max(1.0, (double)s.n / 256.0);
-        const double cost = (2.0 * s.H - 1.0) * ops * rows;
+        const double levels = items[i].kind == BATCH_SWEPT ? 2.0 * s.H - 1.0 : 1.0;
+        const double cost = levels * level_cost(items[i].p->desc.eq) * rows;
+        if ((int64_t)keys.size() + s.n_phases >= ((int64_t)1 << 30))
+            return fail(SWP_EINVAL, "batch too large for one launch");
         for (int64_t ph = 0; ph < s.n_phases; ++ph) keys.push_back(Key{(double)ph * cost, (int)i, (int)ph});
     }
     std::stable_sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
         return x.start < y.start || (x.start == y.start && x.phase < y.phase);
     });
-    std::vector<int2> tasks(keys.size());
-    for (size_t t = 0; t < keys.size(); ++t) tasks[t] = make_int2(keys[t].inst, keys[t].phase);
-    if (tasks.size() >= (size_t)1 << 30 || flags >= (int64_t)1 << 30)
-        return fail(SWP_EINVAL, "batch too large for one launch");
-    swp_status st;
-    if ((st = grow(&b->insts, &b->insts_cap, sizeof(BatchInst<R>) * insts.size())) != SWP_OK) return st;
-    if ((st = grow((void**)&b->tasks, &b->tasks_cap, sizeof(int2) * tasks.size())) != SWP_OK) return st;
-    if ((st = grow((void**)&b->ctr, &b->ctr_cap, sizeof(int) * (tasks.size() + 2))) != SWP_OK) return st;
-    if ((st = grow((void**)&b->flags, &b->flags_cap, sizeof(uint32_t) * (size_t)flags)) != SWP_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(b->insts, insts.data(), sizeof(BatchInst<R>) * insts.size(),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->tasks, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ctr, 0, sizeof(int) * (tasks.size() + 2), b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "batch table upload");
-    // the staging vectors die at return: wait for the copies out of them
-    e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "batch table upload");
+    if (flags >= (int64_t)1 << 30) return fail(SWP_EINVAL, "batch too large for one launch");
+    const size_t ntasks = keys.size();
+    const size_t inst_bytes = sizeof(BatchInst<R>) * insts.size();
+    const size_t task_bytes = sizeof(int2) * ntasks;
+
+    BatchGraph gnew;
+    BatchTables& t = graph ? gnew.t : b->t;
+    swp_status st = grow_tables(t, inst_bytes, ntasks, (size_t)flags);
+    if (st != SWP_OK) {
+        if (graph) gnew.t.release();
+        return st;
+    }
+    // upload through the pinned staging buffer once its previous upload is done
+    cudaError_t e = cudaEventSynchronize(b->staged);
+    if (e == cudaSuccess && b->stage_cap < inst_bytes + task_bytes) {
+        if (b->stage) cudaFreeHost(b->stage);
+        b->stage = nullptr;
+        b->stage_cap = 0;
+        const size_t want = inst_bytes + task_bytes + (inst_bytes + task_bytes) / 2 + 256;
+        e = cudaMallocHost(&b->stage, want);
+        if (e == cudaSuccess) b->stage_cap = want;
+    }
+    if (e == cudaSuccess) {
+        unsigned char* stg = (unsigned char*)b->stage;
+        std::memcpy(stg, insts.data(), inst_bytes);
+        int2* tk = (int2*)(stg + inst_bytes);
+        for (size_t i = 0; i < ntasks; ++i) tk[i] = make_int2(keys[i].inst, keys[i].phase);
+        e = cudaMemcpyAsync(t.insts, stg, inst_bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.tasks, tk, task_bytes, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->staged, b->stream);
+    }
+    if (e != cudaSuccess) {
+        if (graph) gnew.t.release();
+        return cuda_fail(e, "batch table upload");
+    }
     BatchWork w;
-    w.tasks = b->tasks;
-    w.cur_task = b->ctr;
-    w.status = b->ctr + 1;
-    w.task_ctr = b->ctr + 2;
-    w.ntasks = (int)tasks.size();
+    w.tasks = t.tasks;
+    w.cur_task = t.ctr;
+    w.task_ctr = t.ctr + 1;
+    w.status = b->status;
+    w.ntasks = (int)ntasks;
     w.smem_bytes = smem;
-    w.flags = b->flags;
+    w.flags = t.flags;
     w.wait_limit_ns = b->wait_limit_ns;
     const int bps = swept_batch_blocks_per_sm<R>(mode, smem, threads);
-    if (bps <= 0) return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
+    if (bps <= 0) {
+        if (graph) gnew.t.release();
+        return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
+    }
     int64_t blocks = (int64_t)b->sms * bps;
-    int64_t items_total = 0;
-    for (auto& it : items) items_total += it.s.n_phases * it.s.K;
     if (blocks > items_total) blocks = items_total;
-    e = launch_swept_batch<R>(mode, (const BatchInst<R>*)b->insts, w, threads, (int)blocks, b->stream);
+    const BatchInst<R>* dinsts = (const BatchInst<R>*)t.insts;
+    if (!graph) {
+        e = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
+        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, dinsts, w, threads, (int)blocks, b->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+    } else {
+        // the uploads above are ordinary stream work; the graph holds the rest
+        if (!b->capture_stream) {
+            e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                gnew.t.release();
+                return cuda_fail(e, "capture stream");
+            }
+        }
+        cudaGraph_t cg = nullptr;
+        e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->capture_stream);
+            if (e1 == cudaSuccess)
+                e1 = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->capture_stream);
+            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, dinsts, w, threads, (int)blocks, b->capture_stream);
+            e = cudaStreamEndCapture(b->capture_stream, &cg);
+            if (e1 != cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gnew.exec, cg, 0);
+        if (cg) cudaGraphDestroy(cg);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gnew.exec, b->stream);
+        if (e != cudaSuccess) {
+            if (gnew.exec) cudaGraphExecDestroy(gnew.exec);
+            cudaStreamSynchronize(b->stream);
+            gnew.t.release();
+            return cuda_fail(e, "batch graph capture");
+        }
+        gnew.key = std::move(key);
+        for (const auto& it : items) {
+            gnew.all.push_back(it.p);
+            if (it.flip) gnew.flip.push_back(it.p);
+        }
+        if (b->graphs.size() >= 8) {
+            // its last replay may still run: wait before freeing its tables
+            cudaStreamSynchronize(b->stream);
+            cudaGraphExecDestroy(b->graphs.front().exec);
+            b->graphs.front().t.release();
+            b->graphs.erase(b->graphs.begin());
+        }
+        b->graphs.push_back(std::move(gnew));
+    }
     b->launches++;
-    if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-    for (auto& it : items) {
+    for (const auto& it : items) {
         it.p->launches++;
-        if (it.s.top & 1) it.p->cur = 1 - it.p->cur;
+        if (it.flip) it.p->cur = 1 - it.p->cur;
     }
     return SWP_OK;
 }
 
-// Time `reps` advances of `steps` timesteps of `count` copies of a problem in
-// one batch at node width n; returns point-updates per second or < 0.
-double time_width(const swp_desc* desc, const void* u0, int count, int64_t steps, int n, int threads,
-                  cudaStream_t stream)
+swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps, int32_t count,
+                         const int32_t* schemes, int default_scheme, const int32_t* points_per_block,
+                         int32_t threads, int32_t launch)
+{
+    if (!b || !problems || !n_steps) return fail(SWP_EINVAL, "batch, problems or n_steps is NULL");
+    if (count < 0) return fail(SWP_EINVAL, "count must be >= 0");
+    if (launch != SWP_LAUNCH_AUTO && launch != SWP_LAUNCH_PERSISTENT && launch != SWP_LAUNCH_GRAPH)
+        return fail(SWP_EINVAL, "batch launch must be SWP_LAUNCH_AUTO, _PERSISTENT or _GRAPH");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
+        return fail(SWP_EINVAL, "current device differs from the batch's device");
+    std::vector<BatchItem> groups[2][2];   // [heat+KS | Euler][dtype]
+    int max_threads = 1024;
+    for (int32_t i = 0; i < count; ++i) {
+        swp_problem* p = problems[i];
+        if (!p) return fail(SWP_EINVAL, "problem %d is NULL", i);
+        if (p->device != b->device) return fail(SWP_EINVAL, "problem %d is on another device", i);
+        if (p->stream != b->stream) return fail(SWP_EINVAL, "problem %d uses another stream than the batch", i);
+        if (n_steps[i] < 0 || n_steps[i] > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps[%d] out of range", i);
+        for (int32_t j = 0; j < i; ++j)
+            if (problems[j] == p) return fail(SWP_EINVAL, "problem %d appears twice", i);
+        int scheme = schemes ? schemes[i] : default_scheme;
+        if (scheme != SWP_CLASSIC && scheme != SWP_SWEPT && scheme != SWP_SCHEME_AUTO)
+            return fail(SWP_EINVAL, "unknown scheme %d for problem %d", scheme, i);
+        if (n_steps[i] == 0) continue;
+        int n = points_per_block ? points_per_block[i] : 0;
+        if (scheme == SWP_SCHEME_AUTO) {
+            int tn = 0;
+            choice_for(p, &scheme, &tn);
+            if (n == 0) n = tn;
+        }
+        BatchItem it;
+        it.p = p;
+        if (scheme == SWP_SWEPT) {
+            if (n == 0) n = width_for(p);
+            if (n == 0) return fail(SWP_EINVAL, "no valid node width for problem %d", i);
+            swp_status st = check_width(p, n);
+            if (st != SWP_OK) return st;
+            it.kind = BATCH_SWEPT;
+            it.s = plan_swept(p, n_steps[i], n);
+            it.flip = (it.s.top & 1) != 0;
+        } else {
+            if (n == 0) n = default_chunk(p);
+            swp_status st = check_chunk(p, n);
+            if (st != SWP_OK) return st;
+            it.kind = BATCH_CLASSIC;
+            it.s = plan_classic(p, n_steps[i], n);
+            it.flip = p->desc.eq == SWP_HEAT && (it.s.T & 1);
+        }
+        groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
+        if (p->desc.eq == SWP_EULER) max_threads = 256;
+    }
+    if (threads == 0) threads = 256;
+    if (threads < 32 || threads > max_threads || threads % 32)
+        return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
+    for (int g = 0; g < 2; ++g)
+        for (int dt = 0; dt < 2; ++dt) {
+            if (groups[g][dt].empty()) continue;
+            const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
+            const int thr = (g == 1 && threads > 256) ? 256 : threads;
+            const bool graph = launch == SWP_LAUNCH_GRAPH;
+            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
+                                          : batch_group<float>(b, groups[g][dt], mode, thr, graph);
+            if (st != SWP_OK) return st;
+        }
+    return SWP_OK;
+}
+
+// Time two advances (the second timed) of `steps` timesteps of `count`
+// copies of a problem in one batch with the given scheme and width; returns
+// point-updates per second, or < 0.
+double time_batch(const swp_desc* desc, const void* u0, int count, int64_t steps, int scheme, int n, int threads)
 {
     std::vector<swp_problem*> probs;
     double rate = -1.0;
@@ -831,19 +1096,22 @@ double time_width(const swp_desc* desc, const void* u0, int count, int64_t steps
     std::vector<int64_t> st(count, steps);
     std::vector<int32_t> nn(count, n);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (swp_batch_create(stream, &b) != SWP_OK) return -1.0;
+    if (swp_batch_create(nullptr, &b) != SWP_OK) return -1.0;
     for (int i = 0; i < count; ++i) {
         swp_problem* p = nullptr;
-        if (swp_create(desc, u0, 0, stream, &p) != SWP_OK) goto done;
+        if (swp_create(desc, u0, 0, nullptr, &p) != SWP_OK) goto done;
         probs.push_back(p);
     }
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
-    if (swp_batch_advance(b, probs.data(), st.data(), count, nn.data(), threads) != SWP_OK) goto done;
-    if (swp_batch_synchronize(b) != SWP_OK) goto done;
-    cudaEventRecord(e0, stream);
-    if (swp_batch_advance(b, probs.data(), st.data(), count, nn.data(), threads) != SWP_OK) goto done;
-    cudaEventRecord(e1, stream);
-    if (swp_batch_synchronize(b) == SWP_OK) {
+    for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, nullptr);
+        if (batch_advance(b, probs.data(), st.data(), count, nullptr, scheme, nn.data(), threads, SWP_LAUNCH_AUTO) !=
+            SWP_OK)
+            goto done;
+        if (rep == 1) cudaEventRecord(e1, nullptr);
+        if (swp_batch_synchronize(b) != SWP_OK) goto done;
+    }
+    {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms > 0.f) rate = (double)count * desc->n_points * steps / (ms * 1e-3);
@@ -854,6 +1122,34 @@ done:
     for (auto* p : probs) swp_destroy(p);
     swp_batch_destroy(b);
     return rate;
+}
+
+// Fastest swept node width (powers of two that fit) for the description.
+swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, int64_t steps, int* best_n,
+                      double* best_rate)
+{
+    swp_problem probe;   // for the width checks only
+    probe.desc = *desc;
+    probe.rad = radius_of(desc->eq);
+    probe.nv = nv_of(desc->eq);
+    probe.sub = desc->eq == SWP_HEAT ? 1 : 2;
+    probe.esize = esize_of(desc->dtype);
+    probe.N = desc->n_points;
+    if (cudaGetDevice(&probe.device) != cudaSuccess) return fail(SWP_EDEVICE, "no CUDA device");
+    const int cap = desc->eq == SWP_EULER ? 1024 : 4096;
+    *best_n = 0;
+    *best_rate = -1.0;
+    for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
+        if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
+        const int threads = desc->eq == SWP_EULER ? 128 : (n >= 512 ? 256 : 128);
+        const double rate = time_batch(desc, u0_host, count, steps, SWP_SWEPT, n, threads);
+        if (rate > *best_rate) {
+            *best_rate = rate;
+            *best_n = n;
+        }
+    }
+    if (*best_n == 0) return fail(SWP_EINVAL, "no node width could be timed for n_points %lld", (long long)probe.N);
+    return SWP_OK;
 }
 
 }  // namespace
@@ -873,6 +1169,13 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out)
         delete b;
         return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
     }
+    e = cudaMalloc((void**)&b->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        swp_batch_destroy(b);
+        return cuda_fail(e, "batch create");
+    }
     *out = b;
     return SWP_OK;
 }
@@ -880,46 +1183,15 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out)
 swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
                              int32_t count, const int32_t* points_per_block, int32_t threads)
 {
-    if (!b || !problems || !n_steps) return fail(SWP_EINVAL, "batch, problems or n_steps is NULL");
-    if (count < 0) return fail(SWP_EINVAL, "count must be >= 0");
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device)
-        return fail(SWP_EINVAL, "current device differs from the batch's device");
-    std::vector<BatchItem> groups[2][2];   // [heat+KS | Euler][dtype]
-    int max_threads = 1024;
-    for (int32_t i = 0; i < count; ++i) {
-        swp_problem* p = problems[i];
-        if (!p) return fail(SWP_EINVAL, "problem %d is NULL", i);
-        if (p->device != b->device) return fail(SWP_EINVAL, "problem %d is on another device", i);
-        if (p->stream != b->stream) return fail(SWP_EINVAL, "problem %d uses another stream than the batch", i);
-        if (n_steps[i] < 0 || n_steps[i] > ((int64_t)1 << 40)) return fail(SWP_EINVAL, "n_steps[%d] out of range", i);
-        for (int32_t j = 0; j < i; ++j)
-            if (problems[j] == p) return fail(SWP_EINVAL, "problem %d appears twice", i);
-        if (n_steps[i] == 0) continue;
-        int n = points_per_block ? points_per_block[i] : 0;
-        if (n == 0) n = width_for(p);
-        if (n == 0) return fail(SWP_EINVAL, "no valid node width for problem %d", i);
-        swp_status st = check_width(p, n);
-        if (st != SWP_OK) return st;
-        BatchItem it;
-        it.p = p;
-        it.s = plan_swept(p, n_steps[i], n);
-        groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
-        if (p->desc.eq == SWP_EULER) max_threads = 256;
-    }
-    if (threads == 0) threads = 256;
-    if (threads < 32 || threads > max_threads || threads % 32)
-        return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
-    for (int g = 0; g < 2; ++g)
-        for (int dt = 0; dt < 2; ++dt) {
-            if (groups[g][dt].empty()) continue;
-            const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
-            const int thr = (g == 1 && threads > 256) ? 256 : threads;
-            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr)
-                                          : batch_group<float>(b, groups[g][dt], mode, thr);
-            if (st != SWP_OK) return st;
-        }
-    return SWP_OK;
+    return batch_advance(b, problems, n_steps, count, nullptr, SWP_SWEPT, points_per_block, threads,
+                         SWP_LAUNCH_AUTO);
+}
+
+swp_status swp_batch_advance_ex(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
+                                int32_t count, const int32_t* schemes, const int32_t* points_per_block,
+                                int32_t threads, int32_t launch)
+{
+    return batch_advance(b, problems, n_steps, count, schemes, SWP_SCHEME_AUTO, points_per_block, threads, launch);
 }
 
 swp_status swp_batch_synchronize(swp_batch* b)
@@ -927,14 +1199,12 @@ swp_status swp_batch_synchronize(swp_batch* b)
     if (!b) return fail(SWP_EINVAL, "batch is NULL");
     cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return cuda_fail(e, "batch synchronize");
-    if (b->ctr) {
-        int st = 0;
-        e = cudaMemcpy(&st, b->ctr + 1, sizeof(int), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(e, "batch status read");
-        if (st != 0) {
-            cudaMemset(b->ctr + 1, 0, sizeof(int));
-            return fail(SWP_ETIMEOUT, "a node's bounded wait gave up; the batch's states are invalid");
-        }
+    int st = 0;
+    e = cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "batch status read");
+    if (st != 0) {
+        cudaMemset(b->status, 0, sizeof(int));
+        return fail(SWP_ETIMEOUT, "a node's bounded wait gave up; the batch's states are invalid");
     }
     return SWP_OK;
 }
@@ -942,10 +1212,16 @@ swp_status swp_batch_synchronize(swp_batch* b)
 swp_status swp_batch_destroy(swp_batch* b)
 {
     if (!b) return SWP_OK;
-    if (b->insts) cudaFree(b->insts);
-    if (b->tasks) cudaFree(b->tasks);
-    if (b->ctr) cudaFree(b->ctr);
-    if (b->flags) cudaFree(b->flags);
+    if (b->stream || b->status) cudaStreamSynchronize(b->stream);
+    b->t.release();
+    for (auto& g : b->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.t.release();
+    }
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->status) cudaFree(b->status);
+    if (b->stage) cudaFreeHost(b->stage);
+    if (b->staged) cudaEventDestroy(b->staged);
     delete b;
     return SWP_OK;
 }
@@ -960,27 +1236,60 @@ swp_status swp_autotune_width(const swp_desc* desc, const void* u0_host, int32_t
     if (!u0_host || !best_n || batch_count <= 0 || steps <= 0)
         return fail(SWP_EINVAL, "u0_host / best_n NULL or count, steps <= 0");
     *best_n = 0;
-    swp_problem probe;   // for the width checks only
+    int n = 0;
+    double rate = 0.0;
+    if ((st = tune_swept(desc, u0_host, batch_count, steps, &n, &rate)) != SWP_OK) return st;
+    *best_n = n;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    Tuned& t = g_tuned[std::make_tuple(desc->eq, desc->dtype, desc->n_points)];
+    t.n_swept = n;
+    if (t.scheme == SWP_SWEPT) t.n = n;
+    return SWP_OK;
+}
+
+swp_status swp_autotune(const swp_desc* desc, const void* u0_host, int32_t batch_count, int64_t steps,
+                        int32_t* best_scheme, int32_t* best_n)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!u0_host || !best_scheme || !best_n || batch_count <= 0 || steps <= 0)
+        return fail(SWP_EINVAL, "u0_host / best_scheme / best_n NULL or count, steps <= 0");
+    *best_scheme = SWP_SWEPT;
+    *best_n = 0;
+    int n = 0;
+    double swept_rate = 0.0;
+    if ((st = tune_swept(desc, u0_host, batch_count, steps, &n, &swept_rate)) != SWP_OK) return st;
+    // classic in the same batched form: chunks of 256 .. 4096 points
+    int cm = 0;
+    double classic_rate = -1.0;
+    swp_problem probe;
     probe.desc = *desc;
-    probe.rad = radius_of(desc->eq);
-    probe.nv = nv_of(desc->eq);
     probe.esize = esize_of(desc->dtype);
     probe.N = desc->n_points;
-    if (cudaGetDevice(&probe.device) != cudaSuccess) return fail(SWP_EDEVICE, "no CUDA device");
-    const int cap = desc->eq == SWP_EULER ? 1024 : 4096;
-    double best = -1.0;
-    for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
-        if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
-        const int threads = desc->eq == SWP_EULER ? 128 : (n >= 512 ? 256 : 128);
-        const double rate = time_width(desc, u0_host, batch_count, steps, n, threads, nullptr);
-        if (rate > best) {
-            best = rate;
-            *best_n = n;
+    probe.device = 0;
+    cudaGetDevice(&probe.device);
+    for (int m = 256; m <= 4096; m *= 4) {
+        const int mm = (int)std::min<int64_t>(m, desc->n_points);
+        if (check_chunk(&probe, mm) != SWP_OK) continue;
+        const double r = time_batch(desc, u0_host, batch_count, steps, SWP_CLASSIC, mm, 256);
+        if (r > classic_rate) {
+            classic_rate = r;
+            cm = mm;
         }
+        if (mm == desc->n_points) break;
     }
-    if (*best_n == 0) return fail(SWP_EINVAL, "no node width could be timed for n_points %lld", (long long)probe.N);
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[std::make_tuple(desc->eq, desc->dtype, desc->n_points)] = *best_n;
+    Tuned& t = g_tuned[std::make_tuple(desc->eq, desc->dtype, desc->n_points)];
+    t.n_swept = n;
+    if (cm > 0 && classic_rate > swept_rate) {
+        t.scheme = SWP_CLASSIC;
+        t.n = cm;
+    } else {
+        t.scheme = SWP_SWEPT;
+        t.n = n;
+    }
+    *best_scheme = t.scheme;
+    *best_n = t.n;
     return SWP_OK;
 }
 
@@ -989,9 +1298,24 @@ swp_status swp_tuned_width(const swp_desc* desc, int32_t* n)
     swp_status st = check_desc(desc);
     if (st != SWP_OK) return st;
     if (!n) return fail(SWP_EINVAL, "n is NULL");
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    auto it = g_tuned.find(std::make_tuple(desc->eq, desc->dtype, desc->n_points));
-    *n = it == g_tuned.end() ? 0 : it->second;
+    Tuned t;
+    *n = tuned_of(*desc, &t) ? t.n_swept : 0;
+    return SWP_OK;
+}
+
+swp_status swp_tuned(const swp_desc* desc, int32_t* scheme, int32_t* n)
+{
+    swp_status st = check_desc(desc);
+    if (st != SWP_OK) return st;
+    if (!scheme || !n) return fail(SWP_EINVAL, "scheme or n is NULL");
+    Tuned t;
+    if (tuned_of(*desc, &t)) {
+        *scheme = t.scheme;
+        *n = t.n;
+    } else {
+        *scheme = SWP_SWEPT;
+        *n = 0;
+    }
     return SWP_OK;
 }
 

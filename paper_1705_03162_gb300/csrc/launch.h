@@ -67,22 +67,31 @@ template <typename R>
 int swept_persistent_blocks_per_sm(int eq, int n, int threads);
 
 // ---------------------------------------------------------------------------
-// Batched swept advance: many independent problems of one precision in one
-// persistent launch (heat and KS together; Euler in its own launch).  Work is a table of (instance, phase)
-// tasks, each instance's phases in order; a block claims one node of the current task at
-// a time, so items are claimed in dependency order, and waits (bounded) for
-// the instance's two neighbouring nodes of the previous phase.
+// Batched advance: many independent problems of one precision in one
+// persistent launch (heat and KS together; Euler in its own launch).  Work is
+// a table of (instance, phase) tasks, each instance's phases in order; a block
+// claims one item (node or chunk) of the current task at a time, so items are
+// claimed in dependency order, and waits (bounded) for the items of the
+// instance's previous phase that it reads.  A swept instance's phase is a
+// triangle / diamond over nodes of n points; a classic instance's phase is
+// one sub-timestep over K chunks (the balanced partition of [0, N)).
 // ---------------------------------------------------------------------------
+enum BatchKind : int { BATCH_SWEPT = 0, BATCH_CLASSIC = 1 };
+
 template <typename R> struct BatchInst {
-    R* A;                 // even-level row of the instance ([nv][N])
-    R* B;                 // odd-level row
+    R* A;                 // swept: even-level row; classic: the state u ([nv][N])
+    R* B;                 // swept: odd-level row; classic: the other row
     int64_t N;
-    int n, H, K, bc;
-    int64_t Q, r, n_phases;
+    int n, H, K, bc;      // classic: n = widest chunk, H unused, K chunks
+    int64_t Q, r, n_phases;  // classic: n_phases = sub-timesteps, Q = r = 0
     int flag_off;         // first flag of this instance
     int eq;               // HEAT or KS (heat / KS launch), EULER
+    int kind;             // BatchKind
     Coefs<R> c;
 };
+
+// Shared memory of a classic batch item over a chunk of m points.
+size_t batch_classic_smem_bytes(int eq, int m, int elem_bytes);
 
 struct BatchWork {
     const int2* tasks;    // (instance, phase), each instance's phases in order
@@ -90,7 +99,7 @@ struct BatchWork {
     int* cur_task;        // first task with unclaimed nodes (zeroed per launch)
     int ntasks;
     size_t smem_bytes;    // dynamic shared memory of the launch (widest node)
-    uint32_t* flags;      // completed phases per (instance, node), zeroed per launch
+    uint32_t* flags;      // completed phases per (instance, node or chunk), zeroed per launch
     int* status;          // != 0: a wait gave up
     uint64_t wait_limit_ns;
 };

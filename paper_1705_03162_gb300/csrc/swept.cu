@@ -475,6 +475,82 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
 }
 
+// Value of variable v at global point g (within rad of [0, N)) of a [NV][N]
+// row, through the boundary condition; read past L1, since other blocks of
+// the launch write the rows.
+template <typename R>
+__device__ __forceinline__ R row_bc_load(const R* row, int64_t g, int64_t N, int bc, int v, const Coefs<R>& c)
+{
+    if (g < 0 || g >= N) {
+        if (bc == DIRICHLET) return g < 0 ? c.ghost_l[v] : c.ghost_r[v];
+        if (bc == PERIODIC) g = g < 0 ? g + N : g - N;
+        else g = g < 0 ? -g : 2 * (N - 1) - g;
+    }
+    return __ldcg(row + v * N + g);
+}
+
+// One (instance, chunk, sub-step) item of a classic instance (Section 5.1:
+// one sub-timestep over the whole grid, here over chunk k of the balanced
+// partition of [0, N) into K chunks).  Even sub-steps read row A, odd ones
+// row B: heat alternates A -> B -> A; KS and Euler run the predictor A -> B
+// and the final step B -> A in place, with base values from A.
+template <typename R, int EQ>
+__device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int64_t p, unsigned char* smem_raw)
+{
+    constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
+    const int64_t N = in.N;
+    const int64_t x0 = (int64_t)k * N / in.K;
+    const int cnt = (int)((int64_t)(k + 1) * N / in.K - x0);
+    const int W = cnt + 2 * RAD;
+    R* sm = reinterpret_cast<R*>(smem_raw);   // [NV][W]: the chunk and its halo
+    const bool even = (p & 1) == 0;
+    const R* src = even ? in.A : in.B;
+    R* dst = even ? in.B : in.A;
+    const int stage = even ? 0 : 1;
+    const int T = blockDim.x;
+    for (int s = threadIdx.x; s < W; s += T) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sm[v * W + s] = row_bc_load(src, x0 - RAD + s, N, in.bc, v, in.c);
+    }
+    __syncthreads();
+    if constexpr (EQ == HEAT) {
+        for (int l = threadIdx.x; l < cnt; l += T)
+            __stcg(dst + x0 + l, heat_point(sm[l], sm[l + 1], sm[l + 2], in.c.fo));
+    } else if constexpr (EQ == KS) {
+        const R a1 = in.c.a1[stage], a4 = in.c.a4[stage], beta = in.c.beta[stage], gam = in.c.gam[stage];
+        for (int l = threadIdx.x; l < cnt; l += T) {
+            const int q = RAD + l;
+            const R base = stage == 0 ? sm[q] : __ldcg(in.A + x0 + l);
+            __stcg(dst + x0 + l, ks_point(sm[q - 2], sm[q - 1], sm[q], sm[q + 1], sm[q + 2], base, a1, a4, beta, gam));
+        }
+    } else {
+        R* P = sm + NV * W;   // pressure of every staged cell
+        R* G = P + W;         // G[v][l]: interface between chunk cells l-1 and l
+        const int GW = cnt + 1;
+        for (int s = threadIdx.x; s < W; s += T) P[s] = euler_pressure(sm[s], sm[W + s], sm[2 * W + s], in.c.gm1);
+        __syncthreads();
+        for (int l = threadIdx.x; l <= cnt; l += T) {
+            const int sb = RAD + l;
+            const R qa[3] = {sm[sb - 1], sm[W + sb - 1], sm[2 * W + sb - 1]};
+            const R qb[3] = {sm[sb], sm[W + sb], sm[2 * W + sb]};
+            R g3[3];
+            euler_interface(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], in.c.gm1, in.c.ggm1, g3);
+            G[l] = g3[0];
+            G[GW + l] = g3[1];
+            G[2 * GW + l] = g3[2];
+        }
+        __syncthreads();
+        const R kh = in.c.kh[stage];
+        for (int l = threadIdx.x; l < cnt; l += T) {
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const R base = stage == 0 ? sm[v * W + RAD + l] : __ldcg(in.A + v * N + x0 + l);
+                __stcg(dst + v * N + x0 + l, euler_update(G[v * GW + l + 1], G[v * GW + l], base, kh));
+            }
+        }
+    }
+}
+
 // MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
 template <typename R, int MODE>
 __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
@@ -505,14 +581,25 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         const int64_t p = tk.y;
         const int k = node_s, K = in.K;
         if (p > 0 && threadIdx.x == 0) {
-            const int odd = (int)(p & 1);
-            const int kl = odd ? (k + K - 1) % K : k;
-            const int kr = odd ? k : (k + 1) % K;
+            // items of the previous phase this one reads: swept, the two
+            // overlapping nodes; classic, the chunk and its neighbours
+            int kl, km, kr;
+            if (in.kind == BATCH_SWEPT) {
+                const int odd = (int)(p & 1);
+                kl = odd ? (k + K - 1) % K : k;
+                kr = odd ? k : (k + 1) % K;
+                km = kl;
+            } else {
+                const bool per = in.bc == PERIODIC;
+                kl = k > 0 ? k - 1 : (per ? K - 1 : k);
+                km = k;
+                kr = k < K - 1 ? k + 1 : (per ? 0 : k);
+            }
             const uint32_t need = (uint32_t)p;
             const uint32_t* f = w.flags + in.flag_off;
             const uint64_t t_start = global_ns();
             uint32_t polls = 0, backoff = 32;
-            while (ld_acquire(f + kl) < need || ld_acquire(f + kr) < need) {
+            while (ld_acquire(f + kl) < need || ld_acquire(f + kr) < need || ld_acquire(f + km) < need) {
                 if (ld_volatile(w.status) != 0 || ++polls > kMaxPolls ||
                     global_ns() - t_start > w.wait_limit_ns) {
                     atomicExch(w.status, 1);
@@ -526,10 +613,14 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         __syncthreads();
         if (abort_s) break;
         if constexpr (MODE == EULER) {
-            batch_item<R, EULER>(in, k, p, smem_raw);
-        } else {
+            if (in.kind == BATCH_SWEPT) batch_item<R, EULER>(in, k, p, smem_raw);
+            else classic_item<R, EULER>(in, k, p, smem_raw);
+        } else if (in.kind == BATCH_SWEPT) {
             if (in.eq == HEAT) batch_item<R, HEAT>(in, k, p, smem_raw);
             else batch_item<R, KS>(in, k, p, smem_raw);
+        } else {
+            if (in.eq == HEAT) classic_item<R, HEAT>(in, k, p, smem_raw);
+            else classic_item<R, KS>(in, k, p, smem_raw);
         }
         __threadfence();
         __syncthreads();
@@ -614,6 +705,15 @@ int batch_bps_mode(size_t smem, int threads)
 }
 
 }  // namespace
+
+size_t batch_classic_smem_bytes(int eq, int m, int elem_bytes)
+{
+    const size_t rad = eq == HEAT ? 1 : 2, nv = eq == EULER ? 3 : 1;
+    const size_t W = (size_t)m + 2 * rad;
+    size_t e = nv * W;
+    if (eq == EULER) e += W + 3 * ((size_t)m + 1);
+    return (size_t)elem_bytes * e;
+}
 
 size_t swept_smem_bytes(int eq, int n, int elem_bytes)
 {

@@ -23,12 +23,13 @@ OK, EINVAL, ENOMEM, EBUDGET, ECUDA, EUNSUPPORTED, ETIMEOUT, EDEVICE = range(8)
 HEAT, KS, EULER = 0, 1, 2
 PERIODIC, REFLECTIVE, DIRICHLET = 0, 1, 2
 F64, F32 = 0, 1
-CLASSIC, SWEPT = 0, 1
+CLASSIC, SWEPT, SCHEME_AUTO = 0, 1, 2
 LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH, LAUNCH_REGISTER = 0, 1, 2, 3, 4
 
 _EQ = {"heat": HEAT, "ks": KS, "euler": EULER}
 _BC = {"periodic": PERIODIC, "reflective": REFLECTIVE, "dirichlet": DIRICHLET}
-_SCHEME = {"classic": CLASSIC, "swept": SWEPT}
+_SCHEME = {"classic": CLASSIC, "swept": SWEPT, "auto": SCHEME_AUTO}
+_SCHEME_NAME = {CLASSIC: "classic", SWEPT: "swept"}
 _LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT,
            "graph": LAUNCH_GRAPH, "register": LAUNCH_REGISTER}
 _DTYPE = {"f64": F64, "f32": F32}
@@ -41,6 +42,7 @@ ABI_SYMBOLS = (
     "swp_status_str", "swp_last_error", "swp_swept_noalloc",
     "swp_batch_create", "swp_batch_advance", "swp_batch_synchronize", "swp_batch_destroy",
     "swp_batch_kernel_launches", "swp_autotune_width", "swp_tuned_width",
+    "swp_batch_advance_ex", "swp_autotune", "swp_tuned",
     "swp_server_create", "swp_server_submit", "swp_server_poll", "swp_server_wait",
     "swp_server_stats", "swp_server_destroy",
 )
@@ -119,11 +121,16 @@ def load_library(path: str = LIB_PATH):
             "swp_batch_create": ([vp, ctypes.POINTER(P)], ctypes.c_int),
             "swp_batch_advance": ([P, ctypes.POINTER(P), ctypes.POINTER(i64), i32,
                                    ctypes.POINTER(i32), i32], ctypes.c_int),
+            "swp_batch_advance_ex": ([P, ctypes.POINTER(P), ctypes.POINTER(i64), i32, ctypes.POINTER(i32),
+                                      ctypes.POINTER(i32), i32, i32], ctypes.c_int),
             "swp_batch_synchronize": ([P], ctypes.c_int),
             "swp_batch_destroy": ([P], ctypes.c_int),
             "swp_batch_kernel_launches": ([P], i64),
             "swp_autotune_width": ([ctypes.POINTER(Desc), vp, i32, i64, ctypes.POINTER(i32)], ctypes.c_int),
             "swp_tuned_width": ([ctypes.POINTER(Desc), ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_autotune": ([ctypes.POINTER(Desc), vp, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                             ctypes.c_int),
+            "swp_tuned": ([ctypes.POINTER(Desc), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "swp_server_create": ([ctypes.POINTER(ServerConfig), vp, ctypes.POINTER(P)], ctypes.c_int),
             "swp_server_submit": ([P, ctypes.POINTER(Desc), vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
             "swp_server_poll": ([P, i64, ctypes.POINTER(i32)], ctypes.c_int),
@@ -292,7 +299,7 @@ def swept_noalloc(spec: ProblemSpec, state, steps: int, n: int = 0, threads: int
 
 
 class Batch:
-    """Batched swept advance: many problems (created with this batch's stream)
+    """Batched advance: many problems (created with this batch's stream)
     advanced together in one persistent launch per (equation, dtype) group."""
 
     def __init__(self, stream=None):
@@ -307,6 +314,17 @@ class Batch:
         st = (ctypes.c_int64 * count)(*[int(x) for x in steps])
         nn = None if n is None else (ctypes.c_int32 * count)(*[int(x) for x in n])
         _check(self._lib.swp_batch_advance(self._h, hs, st, count, nn, int(threads)), "batch_advance")
+
+    def advance_ex(self, problems, steps, schemes=None, n=None, threads: int = 0, launch: str = "auto"):
+        """Per-problem scheme ("swept", "classic" or "auto"; None = all auto)
+        and width (node or chunk); launch "auto" or "graph"."""
+        count = len(problems)
+        hs = (ctypes.c_void_p * count)(*[p._h.value for p in problems])
+        st = (ctypes.c_int64 * count)(*[int(x) for x in steps])
+        sc = None if schemes is None else (ctypes.c_int32 * count)(*[_SCHEME[x] for x in schemes])
+        nn = None if n is None else (ctypes.c_int32 * count)(*[int(x) for x in n])
+        _check(self._lib.swp_batch_advance_ex(self._h, hs, st, count, sc, nn, int(threads), _LAUNCH[launch]),
+               "batch_advance_ex")
 
     def synchronize(self):
         _check(self._lib.swp_batch_synchronize(self._h), "batch_synchronize")
@@ -349,6 +367,25 @@ def tuned_width(spec: ProblemSpec, dtype: str = "f64") -> int:
     _check(load_library().swp_tuned_width(ctypes.byref(make_desc(spec, dtype)), ctypes.byref(out)),
            "tuned_width")
     return out.value
+
+
+def autotune(spec: ProblemSpec, u0: np.ndarray, count: int = 16, steps: int = 200, dtype: str = "f64"):
+    """Time the swept widths and the classic scheme in batches of ``count``
+    copies; keep the faster for this (equation, dtype, N).  Returns
+    (scheme name, width)."""
+    lib = load_library()
+    u0 = np.ascontiguousarray(u0)
+    sc, n = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib.swp_autotune(ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data, int(count), int(steps),
+                            ctypes.byref(sc), ctypes.byref(n)), "autotune")
+    return _SCHEME_NAME[sc.value], n.value
+
+
+def tuned(spec: ProblemSpec, dtype: str = "f64"):
+    sc, n = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load_library().swp_tuned(ctypes.byref(make_desc(spec, dtype)), ctypes.byref(sc), ctypes.byref(n)),
+           "tuned")
+    return _SCHEME_NAME[sc.value], n.value
 
 
 class Server:

@@ -100,3 +100,126 @@ def test_autotune_picks_a_valid_width():
     n = S.autotune_width(spec, u0, count=8, steps=64)
     assert n >= 32 and 8192 % n == 0 and n % 8 == 0
     assert S.tuned_width(spec) == n
+
+
+def _classic_mix(seed=5, count=25):
+    """Classic instances of every supported pairing, ragged sizes, chunk widths
+    from the smallest (4) to the whole grid, FP64 and FP32."""
+    rng = np.random.default_rng(seed)
+    combos = [("heat", "periodic"), ("heat", "reflective"), ("ks", "periodic"), ("euler", "dirichlet"),
+              ("euler", "periodic")]
+    cases = []
+    for i in range(count):
+        eq, bc = combos[i % 5]
+        N = int(rng.integers(100, 2500))
+        steps = int(rng.integers(1, 90))
+        m = [0, 4, 100, 256, N][(i // 5) % 5]
+        dtype = "f32" if (eq != "euler" and i % 3 == 0) else "f64"
+        cases.append((eq, bc, N, steps, m, dtype))
+    return cases
+
+
+def _solo_and_oracle(eq, bc, N, steps, dtype, spec, u0, got, scheme):
+    with S.Problem(spec, u0, dtype) as q:
+        q.advance(steps, scheme)
+        alone = q.read()
+    assert np.array_equal(got, alone), (eq, bc, N, steps, dtype, scheme)
+    ref = u0.copy()
+    O.classic(oprob(spec), ref, steps)
+    assert np.array_equal(got, ref), (eq, bc, N, steps, dtype, scheme)
+
+
+def test_batch_classic_items_match_single_and_oracle():
+    """Classic instances (one phase per sub-timestep, chunks of the balanced
+    partition) beside swept ones in the same launches."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    classic = _classic_mix()
+    swept = _mix(seed=11, count=12)
+    probs, inputs, schemes, widths, steps = [], [], [], [], []
+    for kind, cases in (("classic", classic), ("swept", swept)):
+        for eq, bc, N, st, n, dtype in cases:
+            spec = spec_for(eq, bc, N)
+            u0 = state_for(spec, np.float64 if dtype == "f64" else np.float32, seed=N + st)
+            inputs.append((kind, eq, bc, N, st, dtype, spec, u0))
+            probs.append(S.Problem(spec, u0, dtype, stream=stream))
+            schemes.append(kind)
+            widths.append(n)
+            steps.append(st)
+    with S.Batch(stream) as b:
+        b.advance_ex(probs, steps, schemes, widths)
+        b.synchronize()
+        assert b.kernel_launches() == 3   # heat+KS FP64, heat+KS FP32, Euler FP64
+    for (kind, eq, bc, N, st, dtype, spec, u0), p in zip(inputs, probs):
+        got = p.read()
+        p.close()
+        _solo_and_oracle(eq, bc, N, st, dtype, spec, u0, got, kind)
+
+
+def test_batch_classic_rejects_bad_chunks():
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    spec = I.heat_spec(200)
+    p = S.Problem(spec, state_for(spec), stream=stream)
+    with S.Batch(stream) as b:
+        for m in (3, 201):
+            with pytest.raises(S.SweptError) as e:
+                b.advance_ex([p], [5], ["classic"], [m])
+            assert e.value.status == S.EINVAL
+        with pytest.raises(S.SweptError):
+            b.advance_ex([p], [5], ["swept"], [12], launch="register")
+    p.close()
+
+
+def test_batch_graph_replays_match_oracle():
+    """The same batch advance captured once per (rows, plans) and replayed:
+    heat with an odd step count changes rows every advance, so two graphs
+    alternate."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    cases = [("heat", "periodic", 1000, 7, 40, "swept"), ("heat", "reflective", 999, 5, 128, "classic"),
+             ("ks", "periodic", 2048, 10, 256, "swept"), ("ks", "periodic", 1500, 3, 0, "classic"),
+             ("euler", "dirichlet", 512, 6, 64, "swept"), ("euler", "periodic", 700, 4, 100, "classic")]
+    probs, inputs = [], []
+    for eq, bc, N, st, n, kind in cases:
+        spec = spec_for(eq, bc, N)
+        u0 = state_for(spec, seed=N)
+        inputs.append((spec, u0))
+        probs.append(S.Problem(spec, u0, stream=stream))
+    reps = 5
+    with S.Batch(stream) as b:
+        for _ in range(reps):
+            b.advance_ex(probs, [c[3] for c in cases], [c[5] for c in cases], [c[4] for c in cases],
+                         launch="graph")
+        b.synchronize()
+        assert b.kernel_launches() == 2 * reps
+    for (eq, bc, N, st, n, kind), (spec, u0), p in zip(cases, inputs, probs):
+        ref = u0.copy()
+        O.classic(oprob(spec), ref, reps * st)
+        assert np.array_equal(p.read(), ref), (eq, bc, N, st, n, kind)
+        p.close()
+
+
+def test_autotune_scheme_and_auto_advances():
+    torch = pytest.importorskip("torch")
+    spec = I.heat_spec(2048)
+    u0 = I.initial_state(spec)
+    scheme, n = S.autotune(spec, u0, count=8, steps=64)
+    assert (scheme, n) == S.tuned(spec)
+    if scheme == "swept":
+        assert 2048 % n == 0 and n % 4 == 0
+    else:
+        assert 4 <= n <= 2048
+    ref = u0.copy()
+    O.classic(oprob(spec), ref, 77)
+    with S.Problem(spec, u0) as p:
+        p.advance(77, "auto")
+        assert np.array_equal(p.read(), ref)
+    stream = torch.cuda.Stream()
+    ps = [S.Problem(spec, u0, stream=stream) for _ in range(3)]
+    with S.Batch(stream) as b:
+        b.advance_ex(ps, [77, 77, 77])
+        b.synchronize()
+    for p in ps:
+        assert np.array_equal(p.read(), ref)
+        p.close()
