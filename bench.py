@@ -45,6 +45,8 @@ KS_FP64_OPS_PER_UPDATE = 14
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal
 # 1.25 TFLOP/s dense FP64 at the maximum SM clock).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
 # a hash of the kernel sources it was taken on; reported as null once the
@@ -393,12 +395,13 @@ def run_gpu(args, wl):
     S.load_library()
 
     spec = I.ks_spec(wl["n_points"])
-    u0_host = I.initial_state(spec)
+    f32 = wl["dtype"] == "f32"
+    u0_host = I.initial_state(spec).astype(np.float32 if f32 else np.float64)
     u0_dev = torch.from_numpy(u0_host).cuda()
     steps = wl["steps"]
     N = spec.n_points
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
-    prob = S.Problem(spec, u0_dev)
+    prob = S.Problem(spec, u0_dev, wl["dtype"])
 
     def one(scheme):
         if scheme == "classic":
@@ -488,7 +491,8 @@ def run_gpu(args, wl):
     flops_per_launch = float(N) * steps * KS_FLOPS_PER_UPDATE / launches_per_solve
     achieved = flops_per_launch / avg_launch_s / 1e12
     ops_rate = float(N) * steps * args.steps * KS_FP64_OPS_PER_UPDATE / t_swept / 1e12
-    key = f"swept_phase_kernel<double,KS> n={wl['points_per_block']} threads={wl['threads']}"
+    peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    key = f"swept_phase_kernel<{'float' if f32 else 'double'},KS> n={wl['points_per_block']} threads={wl['threads']}"
     traffic = None
     rec = NCU_TRAFFIC.get(key)
     if rec and rec.get("src") == _kernel_src_hash():
@@ -500,8 +504,9 @@ def run_gpu(args, wl):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_swept / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "KS N=2^20 FP64 10^4 steps (dx=0.5, dt=0.005, u0=cos(x/16)(1+sin(x/16)))",
+        "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
+        "config": {"workload": f"KS N=2^20 {'FP32' if f32 else 'FP64'} 10^4 steps (dx=0.5, dt=0.005, "
+                               "u0=cos(x/16)(1+sin(x/16)))",
                    "n_points": N, "timesteps": steps, "scheme": "swept",
                    "points_per_block": wl["points_per_block"], "launch": wl["launch"],
                    "parallelism": f"replicas x{world}",
@@ -513,12 +518,13 @@ def run_gpu(args, wl):
                     "swept_speedup_vs_graph": value / classic_graph_value},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
                 "d2h_bytes_per_step": int(u0_host.nbytes)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": key, "flops_per_update": KS_FLOPS_PER_UPDATE,
-                     "fp64_ops_per_update": KS_FP64_OPS_PER_UPDATE,
-                     "fp64_pipe_frac": ops_rate / (FP64_PEAK_TFLOPS / 2),
-                     "peak_note": "FP64 pipe derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+                     ("fp32_ops_per_update" if f32 else "fp64_ops_per_update"): KS_FP64_OPS_PER_UPDATE,
+                     ("fp32_pipe_frac" if f32 else "fp64_pipe_frac"): ops_rate / (peak / 2),
+                     "peak_note": ("FP32 pipe derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz" if f32 else
+                                   "FP64 pipe derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")},
         "gpu_launches": int(launches_swept),
         "clocks": clk,
     }
@@ -643,6 +649,8 @@ def main():
     ap.add_argument("--launch", choices=["per_phase", "persistent", "auto"], default=DEFAULT_WORKLOAD["launch"])
     ap.add_argument("--threads", type=int, default=None)
     ap.add_argument("--timesteps", type=int, default=None)
+    ap.add_argument("--dtype", choices=["f64", "f32"], default=DEFAULT_WORKLOAD["dtype"],
+                    help="precision of the timed KS workload (FP64 is the benchmark; FP32 is the variant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="print the per-size sweep lines instead")
     ap.add_argument("--bandwidth", action="store_true", help="print the classic FP32 bandwidth lines instead")
@@ -655,7 +663,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = dict(DEFAULT_WORKLOAD, launch=args.launch)
+    wl = dict(DEFAULT_WORKLOAD, launch=args.launch, dtype=args.dtype)
     for key, val in (("points_per_block", args.points_per_block), ("threads", args.threads),
                      ("steps", args.timesteps)):
         if val is not None:

@@ -512,7 +512,12 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     swp_status st = check_width(p, n);
     if (st != SWP_OK) return st;
     int threads = o.threads;
-    if (threads == 0) threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
+    if (threads == 0) {
+        if (p->desc.dtype == SWP_F32)   // about 8 points per thread (register-blocked levels)
+            threads = std::max(64, std::min(256, n / 8)) / 32 * 32;
+        else
+            threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
+    }
     const int max_threads = p->desc.eq == SWP_EULER ? 256 : 1024;
     if (threads < 32 || threads > max_threads || threads % 32)
         return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
@@ -954,7 +959,10 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     w.smem_bytes = smem;
     w.flags = t.flags;
     w.wait_limit_ns = b->wait_limit_ns;
-    const int bps = swept_batch_blocks_per_sm<R>(mode, smem, threads);
+    bool reg = false;
+    for (const auto& it : items)
+        if (it.kind == BATCH_SWEPT && swept_reg_slots(it.p->desc.eq, it.s.n, threads, it.p->esize) > 0) reg = true;
+    const int bps = swept_batch_blocks_per_sm<R>(mode, reg, smem, threads);
     if (bps <= 0) {
         if (graph) gnew.t.release();
         return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
@@ -965,7 +973,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     if (!graph) {
         e = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
-        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, dinsts, w, threads, (int)blocks, b->stream);
+        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     } else {
         // the uploads above are ordinary stream work; the graph holds the rest
@@ -982,7 +990,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
             cudaError_t e1 = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->capture_stream);
             if (e1 == cudaSuccess)
                 e1 = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->capture_stream);
-            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, dinsts, w, threads, (int)blocks, b->capture_stream);
+            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->capture_stream);
             e = cudaStreamEndCapture(b->capture_stream, &cg);
             if (e1 != cudaSuccess) e = e1;
         }
@@ -1069,14 +1077,15 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
         groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
         if (p->desc.eq == SWP_EULER) max_threads = 256;
     }
-    if (threads == 0) threads = 256;
-    if (threads < 32 || threads > max_threads || threads % 32)
-        return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
+    if (threads < 0 || threads > max_threads || threads % 32)
+        return fail(SWP_EINVAL, "threads must be 0 or a multiple of 32 in [32, %d]", max_threads);
     for (int g = 0; g < 2; ++g)
         for (int dt = 0; dt < 2; ++dt) {
             if (groups[g][dt].empty()) continue;
             const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
-            const int thr = (g == 1 && threads > 256) ? 256 : threads;
+            // default block: 256 threads, 128 for FP32 (register-blocked levels)
+            int thr = threads ? threads : (dt == SWP_F32 ? 128 : 256);
+            if (g == 1 && thr > 256) thr = 256;
             const bool graph = launch == SWP_LAUNCH_GRAPH;
             swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
                                           : batch_group<float>(b, groups[g][dt], mode, thr, graph);
@@ -1141,7 +1150,7 @@ swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, 
     *best_rate = -1.0;
     for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
         if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
-        const int threads = desc->eq == SWP_EULER ? 128 : (n >= 512 ? 256 : 128);
+        const int threads = (desc->eq == SWP_EULER || desc->dtype == SWP_F32) ? 128 : (n >= 512 ? 256 : 128);
         const double rate = time_batch(desc, u0_host, count, steps, SWP_SWEPT, n, threads);
         if (rate > *best_rate) {
             *best_rate = rate;

@@ -104,12 +104,20 @@ struct BatchWork {
     uint64_t wait_limit_ns;
 };
 
-// mode: HEAT for a heat / KS launch, EULER for an Euler launch
+// mode: HEAT for a heat / KS launch, EULER for an Euler launch.  reg: the
+// heat / KS launch runs its nodes' levels register-blocked where
+// swept_reg_slots allows (nodes next to non-periodic ends stay in shared
+// memory).
 template <typename R>
-cudaError_t launch_swept_batch(int mode, const BatchInst<R>* insts, const BatchWork& w, int threads,
+cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
                                int blocks, cudaStream_t s);
 
 template <typename R>
-int swept_batch_blocks_per_sm(int mode, size_t smem_bytes, int threads);
+int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads);
+
+// Slots per thread of the register-blocked swept levels for node width n and
+// block size threads (2, 4, 8 or, FP32, 16), or 0 when the levels run in
+// shared memory (Euler, or n not split that way).
+int swept_reg_slots(int eq, int n, int threads, int elem_bytes);
 
 }  // namespace swp

@@ -232,6 +232,110 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
     }
 }
 
+// One level of the register-blocked form (below), of parity ODD: odd levels
+// hold predictor values (KS stage 0, base = the source value), even levels the
+// heat step or the KS final values (stage 1, base = the level-j-2 value of the
+// same slot, i.e. the destination register before it is overwritten).
+template <typename R, int EQ, int P, bool ODD>
+__device__ __forceinline__ void reg_level(const R (&src)[P], R (&dst)[P], R* xb, const R (&hl)[Shape<EQ>::RAD],
+                                          const R (&hr)[Shape<EQ>::RAD], int j, int H, int cs, int s0,
+                                          const Coefs<R>& c)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int w = RAD * (j <= H ? j : 2 * H - j);
+    const int lo = cs - w, hi = cs + w;   // slots of level j
+    // source values of the RAD slots left and right of this thread's range
+    R L[RAD], Rt[RAD];
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) {
+        L[k] = __shfl_up_sync(0xffffffffu, src[P - RAD + k], 1);
+        Rt[k] = __shfl_down_sync(0xffffffffu, src[k], 1);
+    }
+    R* x = xb + (ODD ? 2 * 32 * RAD : 0);   // [warp][first | last][RAD]
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < RAD; ++k) x[(2 * warp) * RAD + k] = src[k];
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < RAD; ++k) x[(2 * warp + 1) * RAD + k] = src[P - RAD + k];
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < RAD; ++k) L[k] = warp > 0 ? x[(2 * warp - 1) * RAD + k] : hl[k];
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < RAD; ++k) Rt[k] = warp < nw - 1 ? x[(2 * warp + 2) * RAD + k] : hr[k];
+    }
+    if (s0 + P <= lo || s0 >= hi) return;   // no slot of this thread on level j
+    constexpr int stage = ODD ? 0 : 1;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        // stencil value at local index i + d
+        auto at = [&](int d) -> R {
+            const int q = i + d;
+            return q < 0 ? L[RAD + q] : (q >= P ? Rt[q - P] : src[q]);
+        };
+        R v;
+        if constexpr (EQ == HEAT) {
+            v = heat_point(at(-1), at(0), at(1), c.fo);
+        } else {
+            const R base = ODD ? src[i] : dst[i];
+            v = ks_point(at(-2), at(-1), at(0), at(1), at(2), base, c.a1[stage], c.a4[stage], c.beta[stage],
+                         c.gam[stage]);
+        }
+        const int q = s0 + i;
+        dst[i] = (q >= lo && q < hi) ? v : dst[i];
+    }
+}
+
+// Register-blocked levels j_lo..j_hi (heat and KS nodes that do not touch a
+// non-periodic end; blockDim.x * P == n).  Thread t keeps slots rad + tP ..
+// rad + tP + P - 1 of both rows in registers; stencil neighbours come from
+// the adjacent lanes by warp shuffle and, at warp edges, through the exchange
+// buffer xb (one barrier per level).  The same point updates in the same
+// order as tile_levels, so the bits are the same; the rows go back to shared
+// memory at the end.  j_lo is always odd (H + 1 or 1, H even).
+template <typename R, int EQ, int P>
+__device__ __forceinline__ void tile_levels_reg(R* row0, R* row1, R* xb, int n, int H, int j_lo, int j_hi,
+                                                const Coefs<R>& c)
+{
+    constexpr int RAD = Shape<EQ>::RAD;
+    static_assert(P >= RAD, "a thread must own at least rad slots");
+    const int cs = n / 2 + RAD;
+    const int s0 = RAD + threadIdx.x * P;
+    R r0[P], r1[P], hl[RAD], hr[RAD];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        r0[i] = row0[s0 + i];
+        r1[i] = row1[s0 + i];
+    }
+    // row 1's window halo, read by the widest level (j = H, even: its source is row 1)
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) {
+        hl[k] = row1[k];
+        hr[k] = row1[n + RAD + k];
+    }
+    for (int j = j_lo; j <= j_hi; j += 2) {
+        reg_level<R, EQ, P, true>(r0, r1, xb, hl, hr, j, H, cs, s0, c);
+        if (j + 1 <= j_hi) reg_level<R, EQ, P, false>(r1, r0, xb, hl, hr, j + 1, H, cs, s0, c);
+    }
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        row0[s0 + i] = r0[i];
+        row1[s0 + i] = r1[i];
+    }
+    __syncthreads();
+}
+
+// Exchange buffer of the register-blocked levels: per level parity, per warp
+// (at most 32), the first and the last rad values of the warp's source row.
+template <int EQ>
+constexpr int kExchangeElems = 2 * 32 * 2 * Shape<EQ>::RAD;
+
 template <int EQ>
 __host__ __device__ __forceinline__ size_t smem_elems(int n)
 {
@@ -239,6 +343,7 @@ __host__ __device__ __forceinline__ size_t smem_elems(int n)
     const size_t W = (size_t)window_width(n, RAD);
     size_t e = 2 * NV * W;
     if (EQ == EULER) e += W + 3 * (W + 1) + 11;
+    else e += kExchangeElems<EQ>;   // warp-edge exchange of the register-blocked levels
     return e;
 }
 
@@ -262,7 +367,23 @@ __device__ __forceinline__ bool node_near_wall(int bc, int k, int K)
     return bc != PERIODIC && (k == 0 || k == K - 1);
 }
 
-template <typename R, int EQ>
+// Levels j_lo..j_hi of one node.  PR > 0: register-blocked with PR slots
+// per thread (heat and KS nodes away from non-periodic ends; blockDim.x * PR
+// == n, the host picks it); otherwise in shared memory.
+template <typename R, int EQ, int PR>
+__device__ __forceinline__ void run_levels(R* row0, R* row1, R* P, R* G, int n, int H, int j_lo, int j_hi,
+                                           int64_t g0, int64_t N, bool wall, int bc, const Coefs<R>& c)
+{
+    if constexpr (PR > 0 && EQ != EULER) {
+        if (!wall) {
+            tile_levels_reg<R, EQ, PR>(row0, row1, P, n, H, j_lo, j_hi, c);
+            return;
+        }
+    }
+    tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, N, wall, bc, c);
+}
+
+template <typename R, int EQ, int PR>
 __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_phase_kernel(R* A, R* B, PhaseGeom g, int bc,
                                                            Coefs<R> c)
 {
@@ -276,7 +397,7 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_phase_kernel(R
     const bool need_b = g.j_lo <= g.H;   // every phase but the first reads odd-level edges
     window_load<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N, need_b);
     __syncthreads();
-    tile_levels<R, EQ>(row0, row1, P, G, g.n, g.H, g.j_lo, g.j_hi, g0, g.N,
+    run_levels<R, EQ, PR>(row0, row1, P, G, g.n, g.H, g.j_lo, g.j_hi, g0, g.N,
                        node_near_wall(bc, k, g.K), bc, c);
     window_store<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N);
 }
@@ -311,7 +432,7 @@ __device__ __forceinline__ uint64_t global_ns()
 // Hard cap on polls of one wait, in case the global timer does not advance.
 constexpr uint32_t kMaxPolls = 1u << 26;
 
-template <typename R, int EQ>
+template <typename R, int EQ, int PR>
 __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_kernel(R* A, R* B, PersistentPlan plan,
                                                                 int bc, Coefs<R> c,
                                                                 uint32_t* flags,
@@ -363,7 +484,7 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_ker
         const int64_t g0 = xc - n / 2 - RAD;
         window_load<R, EQ, true>(A, B, row0, row1, n, g0, plan.N, j_lo <= H);
         __syncthreads();
-        tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, plan.N,
+        run_levels<R, EQ, PR>(row0, row1, P, G, n, H, j_lo, j_hi, g0, plan.N,
                            node_near_wall(bc, k, K), bc, c);
         window_store<R, EQ, true>(A, B, row0, row1, n, g0, plan.N);
         __threadfence();
@@ -454,8 +575,10 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
     return v;
 }
 
-// One (instance, node, phase) item of a batch.
-template <typename R, int EQ>
+// One (instance, node, phase) item of a batch.  REG: heat / KS nodes away
+// from non-periodic ends run register-blocked at n / blockDim.x slots per
+// thread when that is 2, 4, 8 (or, FP32, 16), else in shared memory.
+template <typename R, int EQ, bool REG>
 __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_t p,
                                            unsigned char* smem_raw)
 {
@@ -470,8 +593,26 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     const int64_t g0 = xc - n / 2 - RAD;
     window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
     __syncthreads();
-    tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
-                       in.bc, in.c);
+    bool done = false;
+    if constexpr (REG && EQ != EULER) {
+        done = !node_near_wall(in.bc, k, in.K);
+        if (done) switch (n / (int)blockDim.x) {
+        case 2: tile_levels_reg<R, EQ, 2>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
+        case 4: tile_levels_reg<R, EQ, 4>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
+        case 8: tile_levels_reg<R, EQ, 8>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
+        case 16:
+            if constexpr (sizeof(R) == 4) {
+                tile_levels_reg<R, EQ, 16>(row0, row1, P, n, H, j_lo, j_hi, in.c);
+                break;
+            }
+            done = false;
+            break;
+        default: done = false; break;
+        }
+    }
+    if (!done)
+        run_levels<R, EQ, 0>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
+                             in.bc, in.c);
     window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
 }
 
@@ -552,7 +693,7 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
 }
 
 // MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
-template <typename R, int MODE>
+template <typename R, int MODE, bool REG>
 __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
                                                                                 BatchWork w)
 {
@@ -613,11 +754,11 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         __syncthreads();
         if (abort_s) break;
         if constexpr (MODE == EULER) {
-            if (in.kind == BATCH_SWEPT) batch_item<R, EULER>(in, k, p, smem_raw);
+            if (in.kind == BATCH_SWEPT) batch_item<R, EULER, false>(in, k, p, smem_raw);
             else classic_item<R, EULER>(in, k, p, smem_raw);
         } else if (in.kind == BATCH_SWEPT) {
-            if (in.eq == HEAT) batch_item<R, HEAT>(in, k, p, smem_raw);
-            else batch_item<R, KS>(in, k, p, smem_raw);
+            if (in.eq == HEAT) batch_item<R, HEAT, REG>(in, k, p, smem_raw);
+            else batch_item<R, KS, REG>(in, k, p, smem_raw);
         } else {
             if (in.eq == HEAT) classic_item<R, HEAT>(in, k, p, smem_raw);
             else classic_item<R, KS>(in, k, p, smem_raw);
@@ -635,14 +776,59 @@ cudaError_t set_smem(const void* fn, size_t smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Slots per thread of the register-blocked levels for node width n and
+// block size threads, or 0 for the shared-memory levels.
+// FP32 only: in FP64 the FP64 pipe bounds both forms, and the register-blocked
+// kernel's larger register file cost (fewer resident nodes) made it slower.
+template <typename R, int EQ>
+int reg_slots(int n, int threads)
+{
+    if (EQ == EULER || sizeof(R) != 4 || threads <= 0 || n % threads) return 0;
+    const int p = n / threads;
+    return (p == 2 || p == 4 || p == 8 || (p == 16 && sizeof(R) == 4)) ? p : 0;
+}
+
+template <typename R, int EQ, int PR>
+cudaError_t phase_launch_pr(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
+                            cudaStream_t s)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(g.n);
+    cudaError_t e = set_smem<R, EQ>((const void*)swept_phase_kernel<R, EQ, PR>, smem);
+    if (e != cudaSuccess) return e;
+    swept_phase_kernel<R, EQ, PR><<<g.K, threads, smem, s>>>(A, B, g, bc, c);
+    return cudaGetLastError();
+}
+
 template <typename R, int EQ>
 cudaError_t phase_launch_eq(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
                             cudaStream_t s)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(g.n);
-    cudaError_t e = set_smem<R, EQ>((const void*)swept_phase_kernel<R, EQ>, smem);
+    if constexpr (EQ != EULER) {
+        switch (reg_slots<R, EQ>(g.n, threads)) {
+        case 2: return phase_launch_pr<R, EQ, 2>(bc, A, B, g, c, threads, s);
+        case 4: return phase_launch_pr<R, EQ, 4>(bc, A, B, g, c, threads, s);
+        case 8: return phase_launch_pr<R, EQ, 8>(bc, A, B, g, c, threads, s);
+        case 16:
+            if constexpr (sizeof(R) == 4) return phase_launch_pr<R, EQ, 16>(bc, A, B, g, c, threads, s);
+            break;
+        default: break;
+        }
+    }
+    return phase_launch_pr<R, EQ, 0>(bc, A, B, g, c, threads, s);
+}
+
+template <typename R, int EQ, int PR>
+cudaError_t persistent_launch_pr(int bc, R* A, R* B, const PersistentPlan& plan, const Coefs<R>& c,
+                                 uint32_t* flags, unsigned int* counter, int* status, int threads,
+                                 int blocks, cudaStream_t s)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(plan.n);
+    cudaError_t e = set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ, PR>, smem);
     if (e != cudaSuccess) return e;
-    swept_phase_kernel<R, EQ><<<g.K, threads, smem, s>>>(A, B, g, bc, c);
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    swept_persistent_kernel<R, EQ, PR><<<blocks, threads, smem, s>>>(A, B, plan, bc, c, flags, counter,
+                                                                      status);
     return cudaGetLastError();
 }
 
@@ -651,26 +837,48 @@ cudaError_t persistent_launch_eq(int bc, R* A, R* B, const PersistentPlan& plan,
                                  uint32_t* flags, unsigned int* counter, int* status, int threads,
                                  int blocks, cudaStream_t s)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(plan.n);
-    cudaError_t e = set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ>, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    swept_persistent_kernel<R, EQ><<<blocks, threads, smem, s>>>(A, B, plan, bc, c, flags, counter,
-                                                                  status);
-    return cudaGetLastError();
+    if constexpr (EQ != EULER) {
+        switch (reg_slots<R, EQ>(plan.n, threads)) {
+        case 2: return persistent_launch_pr<R, EQ, 2>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
+        case 4: return persistent_launch_pr<R, EQ, 4>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
+        case 8: return persistent_launch_pr<R, EQ, 8>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
+        case 16:
+            if constexpr (sizeof(R) == 4)
+                return persistent_launch_pr<R, EQ, 16>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
+            break;
+        default: break;
+        }
+    }
+    return persistent_launch_pr<R, EQ, 0>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
+}
+
+template <typename R, int EQ, int PR>
+int persistent_bps_pr(int n, int threads)
+{
+    const size_t smem = sizeof(R) * smem_elems<EQ>(n);
+    if (set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ, PR>, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_persistent_kernel<R, EQ, PR>, threads,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return nb;
 }
 
 template <typename R, int EQ>
 int persistent_bps_eq(int n, int threads)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(n);
-    if (set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ>, smem) != cudaSuccess) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_persistent_kernel<R, EQ>, threads,
-                                                      smem) != cudaSuccess)
-        return 0;
-    return nb;
+    if constexpr (EQ != EULER) {
+        switch (reg_slots<R, EQ>(n, threads)) {
+        case 2: return persistent_bps_pr<R, EQ, 2>(n, threads);
+        case 4: return persistent_bps_pr<R, EQ, 4>(n, threads);
+        case 8: return persistent_bps_pr<R, EQ, 8>(n, threads);
+        case 16:
+            if constexpr (sizeof(R) == 4) return persistent_bps_pr<R, EQ, 16>(n, threads);
+            break;
+        default: break;
+        }
+    }
+    return persistent_bps_pr<R, EQ, 0>(n, threads);
 }
 
 template <typename R, int EQ>
@@ -683,22 +891,22 @@ cudaError_t register_launch_eq(R* A, R* B, const PhaseGeom& g, const Coefs<R>& c
     return cudaGetLastError();
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool REG>
 cudaError_t batch_launch_mode(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
                               cudaStream_t s)
 {
-    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE>, w.smem_bytes);
+    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, w.smem_bytes);
     if (e != cudaSuccess) return e;
-    swept_batch_kernel<R, MODE><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
+    swept_batch_kernel<R, MODE, REG><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
     return cudaGetLastError();
 }
 
-template <typename R, int MODE>
+template <typename R, int MODE, bool REG>
 int batch_bps_mode(size_t smem, int threads)
 {
-    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE>, smem) != cudaSuccess) return 0;
+    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE, REG>, threads, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -784,30 +992,39 @@ cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const 
 }
 
 template <typename R>
-cudaError_t launch_swept_batch(int mode, const BatchInst<R>* insts, const BatchWork& w, int threads,
+cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
                                int blocks, cudaStream_t s)
 {
-    if (mode == EULER) return batch_launch_mode<R, EULER>(insts, w, threads, blocks, s);
-    return batch_launch_mode<R, HEAT>(insts, w, threads, blocks, s);
+    if (mode == EULER) return batch_launch_mode<R, EULER, false>(insts, w, threads, blocks, s);
+    if (reg) return batch_launch_mode<R, HEAT, true>(insts, w, threads, blocks, s);
+    return batch_launch_mode<R, HEAT, false>(insts, w, threads, blocks, s);
 }
 
 template <typename R>
-int swept_batch_blocks_per_sm(int mode, size_t smem_bytes, int threads)
+int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads)
 {
-    if (mode == EULER) return batch_bps_mode<R, EULER>(smem_bytes, threads);
-    return batch_bps_mode<R, HEAT>(smem_bytes, threads);
+    if (mode == EULER) return batch_bps_mode<R, EULER, false>(smem_bytes, threads);
+    if (reg) return batch_bps_mode<R, HEAT, true>(smem_bytes, threads);
+    return batch_bps_mode<R, HEAT, false>(smem_bytes, threads);
 }
 
-template cudaError_t launch_swept_batch<double>(int, const BatchInst<double>*, const BatchWork&, int,
+int swept_reg_slots(int eq, int n, int threads, int elem_bytes)
+{
+    if (eq == EULER) return 0;
+    if (elem_bytes == 4) return eq == HEAT ? reg_slots<float, HEAT>(n, threads) : reg_slots<float, KS>(n, threads);
+    return eq == HEAT ? reg_slots<double, HEAT>(n, threads) : reg_slots<double, KS>(n, threads);
+}
+
+template cudaError_t launch_swept_batch<double>(int, bool, const BatchInst<double>*, const BatchWork&, int,
                                                 int, cudaStream_t);
-template cudaError_t launch_swept_batch<float>(int, const BatchInst<float>*, const BatchWork&, int,
+template cudaError_t launch_swept_batch<float>(int, bool, const BatchInst<float>*, const BatchWork&, int,
                                                int, cudaStream_t);
 template cudaError_t launch_swept_register<double>(int, double*, double*, const PhaseGeom&,
                                                    const Coefs<double>&, int, cudaStream_t);
 template cudaError_t launch_swept_register<float>(int, float*, float*, const PhaseGeom&,
                                                   const Coefs<float>&, int, cudaStream_t);
-template int swept_batch_blocks_per_sm<double>(int, size_t, int);
-template int swept_batch_blocks_per_sm<float>(int, size_t, int);
+template int swept_batch_blocks_per_sm<double>(int, bool, size_t, int);
+template int swept_batch_blocks_per_sm<float>(int, bool, size_t, int);
 template int swept_persistent_blocks_per_sm<double>(int, int, int);
 template int swept_persistent_blocks_per_sm<float>(int, int, int);
 
