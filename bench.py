@@ -237,7 +237,7 @@ def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
         for eq in ("heat", "ks"):
             for e in range(10, 17):
                 spec, u0 = _spec_ic(eq, 2 ** e, npdt)
-                tuned[(eq, e)] = S.autotune(spec, u0, count=32, steps=256, dtype=dtype)
+                tuned[(eq, e)] = S.autotune(spec, u0, count=256, steps=128, dtype=dtype)
         tune_s = time.perf_counter() - t0
         stream = torch.cuda.Stream()
         probs, schemes, widths = [], [], []
@@ -664,6 +664,8 @@ def main():
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     wl = dict(DEFAULT_WORKLOAD, launch=args.launch, dtype=args.dtype)
+    if args.dtype == "f32":
+        wl["threads"] = 128   # 8 slots per thread: the register-blocked FP32 levels
     for key, val in (("points_per_block", args.points_per_block), ("threads", args.threads),
                      ("steps", args.timesteps)):
         if val is not None:

@@ -1083,8 +1083,9 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
         for (int dt = 0; dt < 2; ++dt) {
             if (groups[g][dt].empty()) continue;
             const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
-            // default block: 256 threads, 128 for FP32 (register-blocked levels)
-            int thr = threads ? threads : (dt == SWP_F32 ? 128 : 256);
+            // default block, measured on the batched heat+KS workload: 128
+            // threads in FP64, 64 in FP32 (register-blocked levels)
+            int thr = threads ? threads : (dt == SWP_F32 ? 64 : 128);
             if (g == 1 && thr > 256) thr = 256;
             const bool graph = launch == SWP_LAUNCH_GRAPH;
             swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
@@ -1150,7 +1151,7 @@ swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, 
     *best_rate = -1.0;
     for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
         if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
-        const int threads = (desc->eq == SWP_EULER || desc->dtype == SWP_F32) ? 128 : (n >= 512 ? 256 : 128);
+        const int threads = desc->dtype == SWP_F32 ? 64 : 128;   // the batch defaults
         const double rate = time_batch(desc, u0_host, count, steps, SWP_SWEPT, n, threads);
         if (rate > *best_rate) {
             *best_rate = rate;
