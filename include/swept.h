@@ -189,7 +189,7 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out);
 /* Advance problems[i] by n_steps[i] timesteps (swept), i < count.
  * points_per_block: per-problem node widths, or NULL / 0 entries for the
  * tuned width of swp_autotune_width (else the default rule).  threads: block
- * size (0 = 128 for FP64 and 64 for FP32; Euler at most 256).  Problems must be distinct.  Asynchronous;
+ * size (0 = 128 for FP64 and 32 for FP32; Euler at most 256).  Problems must be distinct.  Asynchronous;
  * SWP_ETIMEOUT surfaces at swp_batch_synchronize. */
 swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
                              int32_t count, const int32_t* points_per_block, int32_t threads);
@@ -217,7 +217,7 @@ int64_t swp_batch_kernel_launches(const swp_batch* b);
 
 /* Node-width autotuner.  Times batch_count copies of the problem (initial
  * state u0_host, host memory) advanced `steps` timesteps in one batch for
- * every power-of-two node width that fits, keeps the fastest for the
+ * every power-of-two node width up to 1024 that fits, keeps the fastest for the
  * (equation, dtype, n_points) of desc, and returns it in best_n.  Later
  * batches use it for problems of that key.  Allocates and frees its own
  * trial problems; synchronises the device. */

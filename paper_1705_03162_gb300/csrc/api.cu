@@ -1084,8 +1084,9 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
             if (groups[g][dt].empty()) continue;
             const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
             // default block, measured on the batched heat+KS workload: 128
-            // threads in FP64, 64 in FP32 (register-blocked levels)
-            int thr = threads ? threads : (dt == SWP_F32 ? 64 : 128);
+            // threads in FP64; one warp per node in FP32, where a level's
+            // barrier is the cost that matters
+            int thr = threads ? threads : (dt == SWP_F32 ? 32 : 128);
             if (g == 1 && thr > 256) thr = 256;
             const bool graph = launch == SWP_LAUNCH_GRAPH;
             swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
@@ -1146,12 +1147,13 @@ swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, 
     probe.esize = esize_of(desc->dtype);
     probe.N = desc->n_points;
     if (cudaGetDevice(&probe.device) != cudaSuccess) return fail(SWP_EDEVICE, "no CUDA device");
-    const int cap = desc->eq == SWP_EULER ? 1024 : 4096;
+    // wider nodes won in isolation but lost in mixed batches (fewer, longer items)
+    const int cap = 1024;
     *best_n = 0;
     *best_rate = -1.0;
     for (int n = 32; n <= cap && n <= probe.N; n *= 2) {
         if (check_width(&probe, n) != SWP_OK || probe.N / n < 2) continue;
-        const int threads = desc->dtype == SWP_F32 ? 64 : 128;   // the batch defaults
+        const int threads = desc->dtype == SWP_F32 ? 32 : 128;   // the batch defaults
         const double rate = time_batch(desc, u0_host, count, steps, SWP_SWEPT, n, threads);
         if (rate > *best_rate) {
             *best_rate = rate;

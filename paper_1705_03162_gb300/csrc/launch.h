@@ -104,10 +104,10 @@ struct BatchWork {
     uint64_t wait_limit_ns;
 };
 
-// mode: HEAT for a heat / KS launch, EULER for an Euler launch.  reg (and at
-// most 256 threads): the heat / KS launch runs its nodes' levels
-// register-blocked where swept_reg_slots allows (nodes next to non-periodic
-// ends stay in shared memory).
+// mode: HEAT for a heat / KS launch, EULER for an Euler launch.  reg: the
+// heat / KS launch runs its nodes' levels register-blocked where
+// swept_reg_slots allows (nodes next to non-periodic ends stay in shared
+// memory).
 template <typename R>
 cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
                                int blocks, cudaStream_t s);

@@ -272,30 +272,23 @@ __device__ __forceinline__ void reg_level(const R (&src)[P], R (&dst)[P], R* xb,
     }
     if (s0 + P <= lo || s0 >= hi) return;   // no slot of this thread on level j
     constexpr int stage = ODD ? 0 : 1;
-    // point i of this thread (local stencil index i + d)
-    auto point = [&](int i) -> R {
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        // stencil value at local index i + d
         auto at = [&](int d) -> R {
             const int q = i + d;
             return q < 0 ? L[RAD + q] : (q >= P ? Rt[q - P] : src[q]);
         };
+        R v;
         if constexpr (EQ == HEAT) {
-            return heat_point(at(-1), at(0), at(1), c.fo);
+            v = heat_point(at(-1), at(0), at(1), c.fo);
         } else {
             const R base = ODD ? src[i] : dst[i];
-            return ks_point(at(-2), at(-1), at(0), at(1), at(2), base, c.a1[stage], c.a4[stage], c.beta[stage],
-                            c.gam[stage]);
+            v = ks_point(at(-2), at(-1), at(0), at(1), at(2), base, c.a1[stage], c.a4[stage], c.beta[stage],
+                         c.gam[stage]);
         }
-    };
-    if (s0 >= lo && s0 + P <= hi) {   // all slots on the level (the common case)
-#pragma unroll
-        for (int i = 0; i < P; ++i) dst[i] = point(i);
-    } else {
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-            const int q = s0 + i;
-            const R v = point(i);
-            dst[i] = (q >= lo && q < hi) ? v : dst[i];
-        }
+        const int q = s0 + i;
+        dst[i] = (q >= lo && q < hi) ? v : dst[i];
     }
 }
 
@@ -701,7 +694,7 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
 
 // MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
 template <typename R, int MODE, bool REG>
-__global__ void __launch_bounds__((MODE == EULER || REG) ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
+__global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
                                                                                 BatchWork w)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1003,7 +996,7 @@ cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, co
                                int blocks, cudaStream_t s)
 {
     if (mode == EULER) return batch_launch_mode<R, EULER, false>(insts, w, threads, blocks, s);
-    if (reg && threads <= 256) return batch_launch_mode<R, HEAT, true>(insts, w, threads, blocks, s);
+    if (reg) return batch_launch_mode<R, HEAT, true>(insts, w, threads, blocks, s);
     return batch_launch_mode<R, HEAT, false>(insts, w, threads, blocks, s);
 }
 
@@ -1011,7 +1004,7 @@ template <typename R>
 int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads)
 {
     if (mode == EULER) return batch_bps_mode<R, EULER, false>(smem_bytes, threads);
-    if (reg && threads <= 256) return batch_bps_mode<R, HEAT, true>(smem_bytes, threads);
+    if (reg) return batch_bps_mode<R, HEAT, true>(smem_bytes, threads);
     return batch_bps_mode<R, HEAT, false>(smem_bytes, threads);
 }
 
