@@ -54,7 +54,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 NCU_TRAFFIC = {
     # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
-    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "3514c6ced65845f1", "bytes_per_launch": 16783872},
+    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "10b4b7352ae120f5", "bytes_per_launch": 16783872},
 }
 
 
