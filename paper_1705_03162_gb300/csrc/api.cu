@@ -535,6 +535,16 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
 
 }  // namespace
 
+namespace swp {
+
+int64_t swept_half_cycle_steps(const swp_problem* p)
+{
+    const int n = width_for(p);
+    if (n <= 0) return 1;
+    return std::max<int64_t>(1, (int64_t)(n / (2 * p->rad)) / p->sub);
+}
+}  // namespace swp
+
 extern "C" {
 
 swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes)

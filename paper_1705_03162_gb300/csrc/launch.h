@@ -7,6 +7,8 @@
 
 #include "scheme.cuh"
 
+struct swp_problem;
+
 namespace swp {
 
 // One sub-timestep of the classic decomposition over all N points (Section
@@ -119,5 +121,9 @@ int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads
 // block size threads (2, 4, 8 or, FP32, 16), or 0 when the levels run in
 // shared memory (Euler, or n not split that way).
 int swept_reg_slots(int eq, int n, int threads, int elem_bytes);
+
+// Timesteps of one swept half-cycle (H levels) at the node width a batch
+// advance of p would use (the tuned or default width).
+int64_t swept_half_cycle_steps(const swp_problem* p);
 
 }  // namespace swp

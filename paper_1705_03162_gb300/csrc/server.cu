@@ -8,7 +8,8 @@
 //    resident on the device until it finishes;
 //  - rounds: every active request advances by a chunk of timesteps sized to
 //    an equal share of a target round time (estimated FP64 work per
-//    point-update of each equation), all in one batched launch per group
+//    point-update of each equation), at least two swept half-cycles of its
+//    node width, all in one batched launch per group
 //    (swp_batch_advance); requests that arrive meanwhile join the next round,
 //    so new and in-flight work overlap on the device;
 //  - retirement: finished requests are copied back to host memory, their
@@ -32,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/swept.h"
+#include "launch.h"
 
 namespace {
 
@@ -137,6 +139,9 @@ swp_status swp_server::round()
     for (auto& r : active) {
         const int64_t left = r->steps_total - r->steps_done;
         int64_t c = (int64_t)(share / ((double)r->desc.n_points * cost_per_update(r->desc)));
+        // at least two swept half-cycles: shorter advances are mostly the
+        // half-efficient opening and closing triangles
+        c = std::max<int64_t>(c, 2 * swp::swept_half_cycle_steps(r->prob));
         c = std::max<int64_t>(1, std::min(c, left));
         probs.push_back(r->prob);
         chunk.push_back(c);
