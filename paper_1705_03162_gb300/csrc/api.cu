@@ -535,16 +535,6 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
 
 }  // namespace
 
-namespace swp {
-
-int64_t swept_half_cycle_steps(const swp_problem* p)
-{
-    const int n = width_for(p);
-    if (n <= 0) return 1;
-    return std::max<int64_t>(1, (int64_t)(n / (2 * p->rad)) / p->sub);
-}
-}  // namespace swp
-
 extern "C" {
 
 swp_status swp_required_bytes(const swp_desc* desc, size_t* bytes)
@@ -824,7 +814,8 @@ struct BatchItem {
     swp_problem* p;
     int kind;       // BATCH_SWEPT / BATCH_CLASSIC
     SweptPlan s;    // swept plan; classic: n = widest chunk, K = chunks, n_phases = sub-steps
-    bool flip;      // the state ends in the other row
+    int64_t p_lo, p_hi;   // phases of the plan this launch runs
+    bool flip;      // the state ends in the other row (the plan's last phase runs)
 };
 
 // Classic instance of a batch: K = ceil(N / m) chunks of the balanced
@@ -865,6 +856,8 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
             key.push_back(it.kind);
             key.push_back(it.s.n);
             key.push_back(it.s.T);
+            key.push_back(it.p_lo);
+            key.push_back(it.p_hi);
         }
         for (auto& g : b->graphs)
             if (g.key == key) {
@@ -892,12 +885,13 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         in.Q = it.s.Q;
         in.r = it.s.r;
         in.n_phases = it.s.n_phases;
+        in.phase_lo = it.p_lo;
         in.flag_off = (int)flags;
         in.eq = it.p->desc.eq;
         in.kind = it.kind;
         in.c = coefs_of<R>(it.p);
         flags += it.s.K;
-        items_total += it.s.n_phases * it.s.K;
+        items_total += (it.p_hi - it.p_lo) * it.s.K;
         smem = std::max(smem, it.kind == BATCH_SWEPT ? swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize)
                                                      : batch_classic_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
     }
@@ -918,9 +912,10 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         const double rows = std::max(1.0, (double)s.n / 256.0);
         const double levels = items[i].kind == BATCH_SWEPT ? 2.0 * s.H - 1.0 : 1.0;
         const double cost = levels * level_cost(items[i].p->desc.eq) * rows;
-        if ((int64_t)keys.size() + s.n_phases >= ((int64_t)1 << 30))
+        const int64_t lo = items[i].p_lo, hi = items[i].p_hi;
+        if ((int64_t)keys.size() + (hi - lo) >= ((int64_t)1 << 30))
             return fail(SWP_EINVAL, "batch too large for one launch");
-        for (int64_t ph = 0; ph < s.n_phases; ++ph) keys.push_back(Key{(double)ph * cost, (int)i, (int)ph});
+        for (int64_t ph = lo; ph < hi; ++ph) keys.push_back(Key{(double)(ph - lo) * cost, (int)i, (int)ph});
     }
     std::stable_sort(keys.begin(), keys.end(), [](const Key& x, const Key& y) {
         return x.start < y.start || (x.start == y.start && x.phase < y.phase);
@@ -1035,6 +1030,25 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     return SWP_OK;
 }
 
+// One group launch per (equation group, dtype) of the given items.
+swp_status launch_groups(swp_batch* b, std::vector<BatchItem> (&groups)[2][2], int threads, bool graph)
+{
+    for (int g = 0; g < 2; ++g)
+        for (int dt = 0; dt < 2; ++dt) {
+            if (groups[g][dt].empty()) continue;
+            const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
+            // default block, measured on the batched heat+KS workload: 128
+            // threads in FP64; one warp per node in FP32, where a level's
+            // barrier is the cost that matters
+            int thr = threads ? threads : (dt == SWP_F32 ? 32 : 128);
+            if (g == 1 && thr > 256) thr = 256;
+            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
+                                          : batch_group<float>(b, groups[g][dt], mode, thr, graph);
+            if (st != SWP_OK) return st;
+        }
+    return SWP_OK;
+}
+
 swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps, int32_t count,
                          const int32_t* schemes, int default_scheme, const int32_t* points_per_block,
                          int32_t threads, int32_t launch)
@@ -1084,26 +1098,14 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
             it.s = plan_classic(p, n_steps[i], n);
             it.flip = p->desc.eq == SWP_HEAT && (it.s.T & 1);
         }
+        it.p_lo = 0;
+        it.p_hi = it.s.n_phases;
         groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
         if (p->desc.eq == SWP_EULER) max_threads = 256;
     }
     if (threads < 0 || threads > max_threads || threads % 32)
         return fail(SWP_EINVAL, "threads must be 0 or a multiple of 32 in [32, %d]", max_threads);
-    for (int g = 0; g < 2; ++g)
-        for (int dt = 0; dt < 2; ++dt) {
-            if (groups[g][dt].empty()) continue;
-            const int mode = g == 1 ? SWP_EULER : SWP_HEAT;
-            // default block, measured on the batched heat+KS workload: 128
-            // threads in FP64; one warp per node in FP32, where a level's
-            // barrier is the cost that matters
-            int thr = threads ? threads : (dt == SWP_F32 ? 32 : 128);
-            if (g == 1 && thr > 256) thr = 256;
-            const bool graph = launch == SWP_LAUNCH_GRAPH;
-            swp_status st = dt == SWP_F64 ? batch_group<double>(b, groups[g][dt], mode, thr, graph)
-                                          : batch_group<float>(b, groups[g][dt], mode, thr, graph);
-            if (st != SWP_OK) return st;
-        }
-    return SWP_OK;
+    return launch_groups(b, groups, threads, launch == SWP_LAUNCH_GRAPH);
 }
 
 // Time two advances (the second timed) of `steps` timesteps of `count`
@@ -1175,6 +1177,44 @@ swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, 
 }
 
 }  // namespace
+
+namespace swp {
+
+int swept_width(const swp_problem* p) { return width_for(p); }
+
+int64_t swept_phase_count(const swp_problem* p, int64_t steps, int n)
+{
+    return plan_swept(p, steps, n).n_phases;
+}
+
+swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads)
+{
+    if (!b || (count > 0 && !ranges)) return fail(SWP_EINVAL, "batch or ranges is NULL");
+    std::vector<BatchItem> groups[2][2];
+    for (int i = 0; i < count; ++i) {
+        const PhaseRange& r = ranges[i];
+        swp_problem* p = r.p;
+        if (!p || p->device != b->device || p->stream != b->stream)
+            return fail(SWP_EINVAL, "range %d: problem NULL or on another device / stream", i);
+        swp_status st = check_width(p, r.n);
+        if (st != SWP_OK) return st;
+        BatchItem it;
+        it.p = p;
+        it.kind = BATCH_SWEPT;
+        it.s = plan_swept(p, r.steps, r.n);
+        if (r.p_lo < 0 || r.p_hi > it.s.n_phases || r.p_lo > r.p_hi)
+            return fail(SWP_EINVAL, "range %d: phases [%lld, %lld) outside the plan", i, (long long)r.p_lo,
+                        (long long)r.p_hi);
+        if (r.p_lo == r.p_hi) continue;
+        it.p_lo = r.p_lo;
+        it.p_hi = r.p_hi;
+        it.flip = r.p_hi == it.s.n_phases && (it.s.top & 1);
+        groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
+    }
+    return launch_groups(b, groups, threads, false);
+}
+
+}  // namespace swp
 
 extern "C" {
 

@@ -6,8 +6,10 @@
 #include <cuda_runtime.h>
 
 #include "scheme.cuh"
+#include "../../include/swept.h"
 
 struct swp_problem;
+struct swp_batch;
 
 namespace swp {
 
@@ -86,6 +88,7 @@ template <typename R> struct BatchInst {
     int64_t N;
     int n, H, K, bc;      // classic: n = widest chunk, H unused, K chunks
     int64_t Q, r, n_phases;  // classic: n_phases = sub-timesteps, Q = r = 0
+    int64_t phase_lo;     // first phase of this launch (the earlier ones ran in earlier launches)
     int flag_off;         // first flag of this instance
     int eq;               // HEAT or KS (heat / KS launch), EULER
     int kind;             // BatchKind
@@ -101,7 +104,7 @@ struct BatchWork {
     int* cur_task;        // first task with unclaimed nodes (zeroed per launch)
     int ntasks;
     size_t smem_bytes;    // dynamic shared memory of the launch (widest node)
-    uint32_t* flags;      // completed phases per (instance, node or chunk), zeroed per launch
+    uint32_t* flags;      // phases completed in this launch per (instance, node or chunk), zeroed per launch
     int* status;          // != 0: a wait gave up
     uint64_t wait_limit_ns;
 };
@@ -122,8 +125,20 @@ int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads
 // shared memory (Euler, or n not split that way).
 int swept_reg_slots(int eq, int n, int threads, int elem_bytes);
 
-// Timesteps of one swept half-cycle (H levels) at the node width a batch
-// advance of p would use (the tuned or default width).
-int64_t swept_half_cycle_steps(const swp_problem* p);
+// Open swept advances in pieces (the serving loop): a range runs phases
+// [p_lo, p_hi) of the swept plan for `steps` timesteps at node width n.
+// Between pieces the problem's two rows hold the open state (triangle edges);
+// it is complete, and bit-identical to one swp_advance of `steps` at width n,
+// after the plan's last phase has run.  All pieces of one problem use the same
+// (steps, n) and run in order on the batch's stream.
+struct PhaseRange {
+    swp_problem* p;
+    int n;
+    int64_t steps;
+    int64_t p_lo, p_hi;
+};
+int swept_width(const swp_problem* p);   // the tuned or default node width
+int64_t swept_phase_count(const swp_problem* p, int64_t steps, int n);
+swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads);
 
 }  // namespace swp

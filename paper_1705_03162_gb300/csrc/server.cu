@@ -6,18 +6,19 @@
 //    device-memory budget and its slot count allow (a request larger than the
 //    whole budget fails with SWP_EBUDGET); an admitted request's state stays
 //    resident on the device until it finishes;
-//  - rounds: every active request advances by a chunk of timesteps sized to
-//    an equal share of a target round time (estimated FP64 work per
-//    point-update of each equation), at least two swept half-cycles of its
-//    node width, all in one batched launch per group
-//    (swp_batch_advance); requests that arrive meanwhile join the next round,
-//    so new and in-flight work overlap on the device;
+//  - rounds: an admitted request's whole solve is one swept plan (node width
+//    fixed at admission) run a few phases at a time, the open triangle
+//    edges staying in its rows between rounds.  Each round gives every
+//    active request an equal share of a target round time as credit
+//    (estimated FP64 work per point-update of its equation) and runs as many
+//    of its next phases as its credit pays for (deficit round robin), all in
+//    one batched launch per group; requests that arrive meanwhile join the
+//    next round, so new and in-flight work overlap on the device;
 //  - retirement: finished requests are copied back to host memory, their
 //    device memory is freed, and waiters are woken.
-// A swept advance always ends on a complete state and chunked advances are
-// bit-identical to one long advance, so a request's result does not depend on
-// what else was in the mix.  The paper has no serving layer; this is the
-// GB300 build's.
+// A request's phases are those of one swept advance of its whole step count,
+// so its result is bit-identical to that advance, whatever else was in the
+// mix.  The paper has no serving layer; this is the GB300 build's.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -45,6 +46,9 @@ struct Request {
     std::vector<unsigned char> u0;       // host copy of the initial state
     std::vector<unsigned char> result;   // host copy of the final state
     int64_t steps_total = 0, steps_done = 0;
+    int n = 0;                           // node width of the request's swept plan
+    int64_t n_phases = 0, phase_next = 0;
+    double phase_cost = 0.0, credit = 0.0;   // estimated FP64 operations
     int state = 0;                       // 0 pending, 1 active, 2 done
     swp_status status = SWP_OK;
     swp_problem* prob = nullptr;
@@ -57,11 +61,14 @@ size_t state_bytes(const swp_desc& d)
     return (size_t)(d.eq == SWP_EULER ? 3 : 1) * (size_t)d.n_points * (d.dtype == SWP_F32 ? 4 : 8);
 }
 
-// Estimated FP64-pipe operations per point-update (FP32: an eighth).
+// Estimated cost of one point-update, in units of which the device runs
+// about 4e11 per second: calibrated from the swept rates measured on GB300 at
+// N = 2^20 (FP64 heat 160, KS 37.9, Euler 2.57 G point-updates/s; FP32
+// heat and KS about 9 and 13 times faster).
 double cost_per_update(const swp_desc& d)
 {
-    const double c = d.eq == SWP_HEAT ? 3.0 : (d.eq == SWP_KS ? 16.0 : 450.0);
-    return d.dtype == SWP_F32 ? c / 8.0 : c;
+    if (d.dtype == SWP_F32) return d.eq == SWP_HEAT ? 0.28 : 0.8;
+    return d.eq == SWP_HEAT ? 2.5 : (d.eq == SWP_KS ? 10.5 : 156.0);
 }
 
 }  // namespace
@@ -119,6 +126,19 @@ void swp_server::admit()
             continue;
         }
         r->prob = p;
+        r->n = swp::swept_width(p);
+        r->n_phases = r->n > 0 ? swp::swept_phase_count(p, r->steps_total, r->n) : 0;
+        if (r->n_phases <= 0) {
+            swp_destroy(p);
+            r->prob = nullptr;
+            r->status = SWP_EINVAL;
+            r->state = 2;
+            r->t_done = Clock::now();
+            cv_done.notify_all();
+            continue;
+        }
+        r->phase_cost = (double)r->desc.n_points * (double)r->steps_total * cost_per_update(r->desc) /
+                        (double)r->n_phases;
         r->bytes = need;
         in_use += need;
         r->u0.clear();
@@ -134,31 +154,48 @@ swp_status swp_server::round()
     // called without mu: the active list only changes on this thread
     const double budget_ops = cfg.round_target_ms * 1e-3 * 4.0e11;
     const double share = budget_ops / (double)active.size();
-    std::vector<swp_problem*> probs;
-    std::vector<int64_t> chunk;
-    for (auto& r : active) {
-        const int64_t left = r->steps_total - r->steps_done;
-        int64_t c = (int64_t)(share / ((double)r->desc.n_points * cost_per_update(r->desc)));
-        // at least two swept half-cycles: shorter advances are mostly the
-        // half-efficient opening and closing triangles
-        c = std::max<int64_t>(c, 2 * swp::swept_half_cycle_steps(r->prob));
-        c = std::max<int64_t>(1, std::min(c, left));
-        probs.push_back(r->prob);
-        chunk.push_back(c);
+    std::vector<swp::PhaseRange> ranges;
+    std::vector<int64_t> take(active.size(), 0);
+    size_t richest = 0;
+    for (size_t i = 0; i < active.size(); ++i) {
+        Request& r = *active[i];
+        r.credit += share;
+        if (r.credit / r.phase_cost > active[richest]->credit / active[richest]->phase_cost) richest = i;
+        take[i] = r.credit > 0.0 ? std::min<int64_t>((int64_t)(r.credit / r.phase_cost), r.n_phases - r.phase_next)
+                                 : 0;
+    }
+    bool any = false;
+    double assigned = 0.0;
+    for (size_t i = 0; i < active.size(); ++i) {
+        any = any || take[i] > 0;
+        assigned += (double)take[i] * active[i]->phase_cost;
+    }
+    if (!any) {   // every credit is short of a phase: run the closest one
+        take[richest] = 1;
+        assigned = active[richest]->phase_cost;
+    }
+    for (size_t i = 0; i < active.size(); ++i) {
+        if (take[i] <= 0) continue;
+        Request& r = *active[i];
+        r.credit -= (double)take[i] * r.phase_cost;
+        ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i]});
     }
     const int64_t l0 = swp_batch_kernel_launches(batch);
-    swp_status st = swp_batch_advance(batch, probs.data(), chunk.data(), (int32_t)probs.size(), nullptr,
-                                      cfg.threads);
+    swp_status st = swp::batch_advance_phases(batch, ranges.data(), (int)ranges.size(), cfg.threads);
     if (st == SWP_OK) st = swp_batch_synchronize(batch);
     launches += swp_batch_kernel_launches(batch) - l0;
     rounds++;
     for (size_t i = 0; i < active.size(); ++i) {
+        Request& r = *active[i];
         if (st != SWP_OK) {
-            active[i]->status = st;
-            active[i]->steps_done = active[i]->steps_total;
-        } else {
-            active[i]->steps_done += chunk[i];
-            point_updates += (double)chunk[i] * (double)active[i]->desc.n_points;
+            r.status = st;
+            r.steps_done = r.steps_total;
+            continue;
+        }
+        r.phase_next += take[i];
+        if (r.phase_next >= r.n_phases) {
+            r.steps_done = r.steps_total;
+            point_updates += (double)r.steps_total * (double)r.desc.n_points;
         }
     }
     return st;

@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         const BatchInst<R>& in = insts[tk.x];
         const int64_t p = tk.y;
         const int k = node_s, K = in.K;
-        if (p > 0 && threadIdx.x == 0) {
+        if (p > in.phase_lo && threadIdx.x == 0) {
             // items of the previous phase this one reads: swept, the two
             // overlapping nodes; classic, the chunk and its neighbours
             int kl, km, kr;
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
                 km = k;
                 kr = k < K - 1 ? k + 1 : (per ? 0 : k);
             }
-            const uint32_t need = (uint32_t)p;
+            const uint32_t need = (uint32_t)(p - in.phase_lo);
             const uint32_t* f = w.flags + in.flag_off;
             const uint64_t t_start = global_ns();
             uint32_t polls = 0, backoff = 32;
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         }
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) st_release(w.flags + in.flag_off + k, (uint32_t)p + 1);
+        if (threadIdx.x == 0) st_release(w.flags + in.flag_off + k, (uint32_t)(p - in.phase_lo) + 1);
     }
 }
 
