@@ -254,3 +254,22 @@ def test_device_buffers_roundtrip():
         p.read(out)
         s.synchronize()
     assert np.array_equal(out.cpu().numpy(), _oracle(spec, u0, 50))
+
+
+@pytest.mark.parametrize("eq,bc", [("heat", "periodic"), ("heat", "reflective"), ("ks", "periodic")])
+@pytest.mark.parametrize("n,threads", [(128, 64), (256, 64), (512, 64), (1024, 64), (256, 32), (512, 256)])
+@pytest.mark.parametrize("launch", ["per_phase", "persistent"])
+def test_fp32_register_blocked_levels(eq, bc, n, threads, launch):
+    """FP32 heat / KS nodes run their levels register-blocked when the block
+    splits the node into 2, 4, 8 or 16 slots per thread (the cases cover each);
+    nodes next to a reflective end keep the shared-memory levels.  Several
+    full cycles plus a remainder; bit-identical to the oracle and to classic."""
+    N, steps = 3072, 2 * (n // 2) + 37
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec, np.float32, seed=n + threads)
+    ref = _oracle(spec, u0, steps)
+    with S.Problem(spec, u0, "f32") as p:
+        p.advance(steps, "swept", n, launch, threads)
+        got = p.read()
+    assert np.array_equal(got, ref), (eq, bc, n, threads, launch)
+    assert np.array_equal(got, _gpu(spec, u0, steps, "f32", "classic"))
