@@ -88,11 +88,14 @@ typedef struct {
 
 /* How swp_advance_ex runs the swept scheme. */
 typedef enum {
-    SWP_LAUNCH_AUTO = 0,        /* library choice */
+    SWP_LAUNCH_AUTO = 0,        /* library choice: PERSISTENT from N = 2^17,
+                                   PER_PHASE below */
     SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
                                    nodes synchronise at kernel boundaries */
-    SWP_LAUNCH_PERSISTENT = 2,  /* one kernel for the whole advance; each node
-                                   waits (bounded) on its two neighbours' flags */
+    SWP_LAUNCH_PERSISTENT = 2,  /* one dataflow kernel for the whole advance
+                                   (the batched kernel with this problem
+                                   alone); each node waits (bounded) on its
+                                   two neighbours of the previous phase */
     SWP_LAUNCH_GRAPH = 3,       /* the per-phase (swept) or per-sub-step (classic)
                                    launches as a CUDA graph, captured on first use
                                    for (scheme, n_steps, width, threads) and

@@ -34,15 +34,12 @@ struct swp_problem {
     size_t bytes = 0;
     Coefs<double> cd{};
     Coefs<float> cf{};
-    // persistent swept launch
-    uint32_t* flags = nullptr;
-    int flags_k = 0;          // capacity of flags
-    int flags_last_k = -1;    // node count the flags were last used with
-    uint32_t flag_base = 0;
+    // persistent swept launch: a batch of this one problem (the dataflow
+    // kernel), with its own status word for bounded-wait failures
+    swp_batch* batch = nullptr;
+    int* status = nullptr;
     int inject_withheld_flags = 0;            // test hook: waits never succeed
     uint64_t wait_limit_ns = 2000000000ull;   // bound of one neighbour wait
-    unsigned int* counter = nullptr;
-    int* status = nullptr;
     // CUDA graphs of launch sequences (SWP_LAUNCH_GRAPH), replayed on `stream`
     struct Graph {
         int scheme, n, threads, cur_before, cur_after;
@@ -165,14 +162,15 @@ swp_status check_width(const swp_problem* p, int n)
 
 // Default node width, from the widths measured fastest on GB300 for single
 // problems: about N / 1024 points for heat and KS (at least 64 and 128, at
-// most 1024) and N / 256 for Euler (64 to 512); the nearest width that
-// divides N, is a multiple of 4 rad and fits shared memory.
-int default_width(const swp_problem* p)
+// most 1024; at most 512 in the persistent dataflow launch) and N / 256 for
+// Euler (64 to 512); the nearest width that divides N, is a multiple of
+// 4 rad and fits shared memory.
+int default_width(const swp_problem* p, bool dataflow = false)
 {
     const int step = 4 * p->rad;
     const bool euler = p->desc.eq == SWP_EULER;
     const int lo = (p->desc.eq == SWP_HEAT || euler) ? 64 : 128;
-    const int cap = euler ? 512 : 1024;
+    const int cap = (euler || dataflow) ? 512 : 1024;
     int64_t target = p->N / (euler ? 256 : 1024);
     if (target < lo) target = lo;
     if (target > cap) target = cap;
@@ -330,67 +328,20 @@ swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads)
     return SWP_OK;
 }
 
-swp_status ensure_persistent_state(swp_problem* p, int K)
-{
-    if (p->flags && p->flags_k >= K) return SWP_OK;
-    if (p->flags) cudaFree(p->flags);
-    p->flags = nullptr;
-    cudaError_t e = cudaMalloc(&p->flags, sizeof(uint32_t) * (size_t)K);
-    if (e != cudaSuccess) return fail(SWP_ENOMEM, "flags: %s", cudaGetErrorString(e));
-    e = cudaMemsetAsync(p->flags, 0, sizeof(uint32_t) * (size_t)K, p->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "flags memset");
-    p->flags_k = K;
-    p->flag_base = 0;
-    if (!p->counter) {
-        e = cudaMalloc(&p->counter, sizeof(unsigned int) + sizeof(int) * 4);
-        if (e != cudaSuccess) return fail(SWP_ENOMEM, "counter: %s", cudaGetErrorString(e));
-        p->status = reinterpret_cast<int*>(p->counter + 1);
-        e = cudaMemsetAsync(p->counter, 0, sizeof(unsigned int) + sizeof(int) * 4, p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "status memset");
-    }
-    return SWP_OK;
-}
+// The persistent launch of one problem is the batched dataflow kernel with
+// this problem alone (defined with the batch code below).
+swp_status persistent_via_batch(swp_problem* p, const SweptPlan& s, int threads);
 
 template <typename R>
 swp_status run_swept_persistent(swp_problem* p, const SweptPlan& s, int threads)
 {
-    swp_status st = ensure_persistent_state(p, s.K);
-    if (st != SWP_OK) return st;
-    // flags count completed phases per node; restart the count when the node
-    // layout changes or the count would wrap
-    if (p->flags_last_k != s.K || (uint64_t)p->flag_base + (uint64_t)s.n_phases >= (1ull << 30)) {
-        cudaError_t e = cudaMemsetAsync(p->flags, 0, sizeof(uint32_t) * (size_t)p->flags_k, p->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "flags reset");
-        p->flag_base = 0;
-        p->flags_last_k = s.K;
+    if (!p->status) {
+        cudaError_t e = cudaMalloc((void**)&p->status, sizeof(int));
+        if (e != cudaSuccess) return fail(SWP_ENOMEM, "status word: %s", cudaGetErrorString(e));
+        e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "status memset");
     }
-    const int64_t total = s.n_phases * (int64_t)s.K;
-    if (total >= ((int64_t)1 << 31)) return fail(SWP_EINVAL, "advance too long for one persistent launch");
-    const int bps = swept_persistent_blocks_per_sm<R>(p->desc.eq, s.n, threads);
-    if (bps <= 0) return fail(SWP_EINVAL, "persistent kernel does not fit (n=%d, threads=%d)", s.n, threads);
-    // enough blocks for about two phases in flight: more would only poll the
-    // flags of phases that cannot start yet
-    int64_t blocks = (int64_t)p->sms * bps;
-    if (blocks > 2 * (int64_t)s.K) blocks = 2 * (int64_t)s.K > p->sms ? 2 * (int64_t)s.K : p->sms;
-    if (blocks > total) blocks = total;
-    PersistentPlan plan;
-    plan.N = p->N;
-    plan.n = s.n;
-    plan.H = s.H;
-    plan.K = s.K;
-    plan.Q = s.Q;
-    plan.r = s.r;
-    plan.n_phases = s.n_phases;
-    plan.flag_base = p->flag_base;
-    plan.wait_offset = p->inject_withheld_flags ? (1u << 30) : 0u;
-    plan.wait_limit_ns = p->wait_limit_ns;
-    cudaError_t e = launch_swept_persistent<R>(p->desc.eq, p->desc.bc, (R*)p->rows[p->cur],
-                                               (R*)p->rows[1 - p->cur], plan, coefs_of<R>(p), p->flags,
-                                               p->counter, p->status, threads, (int)blocks, p->stream);
-    p->launches++;
-    if (e != cudaSuccess) return cuda_fail(e, "persistent swept launch");
-    p->flag_base += (uint32_t)s.n_phases;
-    return SWP_OK;
+    return persistent_via_batch(p, s, threads);
 }
 
 // Reads the device status word of persistent launches (stream must be idle).
@@ -402,7 +353,6 @@ swp_status check_device_status(swp_problem* p)
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     if (st != 0) {
         cudaMemset(p->status, 0, sizeof(int));
-        p->flags_last_k = -1;   // flags are inconsistent: restart them next time
         return fail(SWP_ETIMEOUT, "a node's bounded wait for its neighbours gave up; the state is invalid");
     }
     return SWP_OK;
@@ -504,9 +454,14 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         if (s.top & 1) p->cur = 1 - p->cur;
         return SWP_OK;
     }
+    // AUTO: the dataflow (persistent) launch from N = 2^17 up, where it
+    // measured faster than per-phase launches; per-phase launches below
+    const int launch = o.launch != SWP_LAUNCH_AUTO ? o.launch
+                                                   : (p->N >= ((int64_t)1 << 17) ? SWP_LAUNCH_PERSISTENT
+                                                                                 : SWP_LAUNCH_PER_PHASE);
     int n = o.points_per_block;
     if (n == 0) {
-        n = default_width(p);
+        n = default_width(p, launch == SWP_LAUNCH_PERSISTENT);
         if (n == 0) return fail(SWP_EINVAL, "no valid node width for n_points %lld", (long long)p->N);
     }
     swp_status st = check_width(p, n);
@@ -523,7 +478,6 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         return fail(SWP_EINVAL, "threads must be a multiple of 32 in [32, %d]", max_threads);
     const SweptPlan s = plan_swept(p, steps, n);
     if (s.T == 0) return SWP_OK;
-    int launch = o.launch == SWP_LAUNCH_AUTO ? SWP_LAUNCH_PER_PHASE : o.launch;
     if (launch == SWP_LAUNCH_GRAPH) return run_graph<R>(p, steps, SWP_SWEPT, n, threads, &s);
     if (launch == SWP_LAUNCH_PERSISTENT) st = run_swept_persistent<R>(p, s, threads);
     else if (launch == SWP_LAUNCH_PER_PHASE) st = run_swept_phases<R>(p, s, threads);
@@ -687,8 +641,8 @@ swp_status swp_destroy(swp_problem* p)
     if (!p) return SWP_OK;
     cudaError_t e = cudaSuccess;
     if (p->rows[0]) e = cudaFree(p->rows[0]);
-    if (p->flags) cudaFree(p->flags);
-    if (p->counter) cudaFree(p->counter);
+    if (p->batch) swp_batch_destroy(p->batch);
+    if (p->status) cudaFree(p->status);
     for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     g_in_use -= p->bytes;
@@ -842,8 +796,12 @@ swp_status check_chunk(const swp_problem* p, int m)
 // Estimated FP64-pipe operations per point of one level (sub-timestep).
 double level_cost(int eq) { return eq == SWP_HEAT ? 3.0 : (eq == SWP_KS ? 7.0 : 100.0); }
 
+// One persistent launch of the items (one equation group and dtype).  status,
+// wait_offset and wait_limit override the batch's status word and bounded-wait
+// settings (the single-problem persistent launch and its test hook).
 template <typename R>
-swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads, bool graph)
+swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads, bool graph,
+                       int* status = nullptr, uint32_t wait_offset = 0, uint64_t wait_limit = 0)
 {
     std::vector<int64_t> key;
     if (graph) {
@@ -959,11 +917,12 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     w.tasks = t.tasks;
     w.cur_task = t.ctr;
     w.task_ctr = t.ctr + 1;
-    w.status = b->status;
+    w.status = status ? status : b->status;
     w.ntasks = (int)ntasks;
     w.smem_bytes = smem;
     w.flags = t.flags;
-    w.wait_limit_ns = b->wait_limit_ns;
+    w.wait_limit_ns = wait_limit ? wait_limit : b->wait_limit_ns;
+    w.wait_offset = wait_offset;
     bool reg = false;
     for (const auto& it : items)
         if (it.kind == BATCH_SWEPT && swept_reg_slots(it.p->desc.eq, it.s.n, threads, it.p->esize) > 0) reg = true;
@@ -1028,6 +987,29 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         if (it.flip) it.p->cur = 1 - it.p->cur;
     }
     return SWP_OK;
+}
+
+swp_status persistent_via_batch(swp_problem* p, const SweptPlan& s, int threads)
+{
+    if (!p->batch) {
+        swp_status st = swp_batch_create(p->stream, &p->batch);
+        if (st != SWP_OK) return st;
+    }
+    std::vector<BatchItem> items(1);
+    items[0].p = p;
+    items[0].kind = BATCH_SWEPT;
+    items[0].s = s;
+    items[0].p_lo = 0;
+    items[0].p_hi = s.n_phases;
+    items[0].flip = false;   // the caller moves the state's row
+    const int mode = p->desc.eq == SWP_EULER ? SWP_EULER : SWP_HEAT;
+    const uint32_t withhold = p->inject_withheld_flags ? (1u << 30) : 0u;
+    const int64_t l0 = p->launches;
+    swp_status st = p->desc.dtype == SWP_F64
+                        ? batch_group<double>(p->batch, items, mode, threads, false, p->status, withhold, p->wait_limit_ns)
+                        : batch_group<float>(p->batch, items, mode, threads, false, p->status, withhold, p->wait_limit_ns);
+    if (st == SWP_OK && p->launches != l0 + 1) p->launches = l0 + 1;
+    return st;
 }
 
 // One group launch per (equation group, dtype) of the given items.

@@ -48,28 +48,6 @@ template <typename R>
 cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
                                   int threads, cudaStream_t s);
 
-// Whole advance in one persistent launch: blocks claim (phase, node) items in
-// order and wait, with a bounded spin, for the two neighbouring nodes of the
-// previous phase.  flags[K] hold completed-phase counts offset by flag_base;
-// status != 0 after the kernel reports a wait that gave up.
-struct PersistentPlan {
-    int64_t N;
-    int n, H, K;
-    int64_t Q, r;          // full-height phases and remainder levels
-    int64_t n_phases;      // phases in this advance
-    uint32_t flag_base;    // flags already hold this many phases per node
-    uint32_t wait_offset;  // 0; a test hook sets it so that no wait can succeed
-    uint64_t wait_limit_ns;  // bound of one neighbour wait (device global timer)
-};
-
-template <typename R>
-cudaError_t launch_swept_persistent(int eq, int bc, R* A, R* B, const PersistentPlan& plan,
-                                    const Coefs<R>& c, uint32_t* flags, unsigned int* work_counter,
-                                    int* status, int threads, int blocks, cudaStream_t s);
-
-template <typename R>
-int swept_persistent_blocks_per_sm(int eq, int n, int threads);
-
 // ---------------------------------------------------------------------------
 // Batched advance: many independent problems of one precision in one
 // persistent launch (heat and KS together; Euler in its own launch).  Work is
@@ -107,6 +85,7 @@ struct BatchWork {
     uint32_t* flags;      // phases completed in this launch per (instance, node or chunk), zeroed per launch
     int* status;          // != 0: a wait gave up
     uint64_t wait_limit_ns;
+    uint32_t wait_offset; // 0; a test hook sets it so that no wait can succeed
 };
 
 // mode: HEAT for a heat / KS launch, EULER for an Euler launch.  reg: the

@@ -432,67 +432,6 @@ __device__ __forceinline__ uint64_t global_ns()
 // Hard cap on polls of one wait, in case the global timer does not advance.
 constexpr uint32_t kMaxPolls = 1u << 26;
 
-template <typename R, int EQ, int PR>
-__global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_persistent_kernel(R* A, R* B, PersistentPlan plan,
-                                                                int bc, Coefs<R> c,
-                                                                uint32_t* flags,
-                                                                unsigned int* counter, int* status)
-{
-    constexpr int RAD = Shape<EQ>::RAD;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ long long item_s;
-    __shared__ int abort_s;
-    R *row0, *row1, *P, *G;
-    smem_rows<R, EQ>(smem_raw, plan.n, row0, row1, P, G);
-    const int64_t total = plan.n_phases * plan.K;
-    const int H = plan.H, n = plan.n, K = plan.K;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            item_s = (long long)atomicAdd(counter, 1u);
-            abort_s = 0;
-        }
-        __syncthreads();
-        const int64_t item = item_s;
-        if (item >= total) break;
-        const int64_t p = item / K;
-        const int k = (int)(item - p * K);
-        const int odd = (int)(p & 1);
-        const int j_lo = p == 0 ? H + 1 : 1;
-        const int j_hi = p < plan.Q ? 2 * H - 1 : (p == plan.Q ? H + (int)plan.r : (int)plan.r);
-        if (p > 0 && threadIdx.x == 0) {
-            // the two nodes of phase p-1 whose windows overlap this one
-            const int kl = odd ? (k + K - 1) % K : k;
-            const int kr = odd ? k : (k + 1) % K;
-            const uint32_t need = plan.flag_base + (uint32_t)p + plan.wait_offset;
-            const uint64_t t_start = global_ns();
-            uint32_t polls = 0, backoff = 32;
-            while ((int32_t)(ld_acquire(flags + kl) - need) < 0 ||
-                   (int32_t)(ld_acquire(flags + kr) - need) < 0) {
-                if (ld_volatile(status) != 0 || ++polls > kMaxPolls ||
-                    global_ns() - t_start > plan.wait_limit_ns) {
-                    atomicExch(status, 1);
-                    abort_s = 1;
-                    break;
-                }
-                __nanosleep(backoff);
-                if (backoff < 1024) backoff *= 2;
-            }
-        }
-        __syncthreads();
-        if (abort_s) break;
-        const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
-        const int64_t g0 = xc - n / 2 - RAD;
-        window_load<R, EQ, true>(A, B, row0, row1, n, g0, plan.N, j_lo <= H);
-        __syncthreads();
-        run_levels<R, EQ, PR>(row0, row1, P, G, n, H, j_lo, j_hi, g0, plan.N,
-                           node_near_wall(bc, k, K), bc, c);
-        window_store<R, EQ, true>(A, B, row0, row1, n, g0, plan.N);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(flags + k, plan.flag_base + (uint32_t)p + 1);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Register variant (Section 5.1): a node is one warp of 32 points; lane l
 // holds window slot rad + l of both level rows in registers, and the odd row's
@@ -736,7 +675,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
                 km = k;
                 kr = k < K - 1 ? k + 1 : (per ? 0 : k);
             }
-            const uint32_t need = (uint32_t)(p - in.phase_lo);
+            const uint32_t need = (uint32_t)(p - in.phase_lo) + w.wait_offset;
             const uint32_t* f = w.flags + in.flag_off;
             const uint64_t t_start = global_ns();
             uint32_t polls = 0, backoff = 32;
@@ -817,70 +756,6 @@ cudaError_t phase_launch_eq(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<
     return phase_launch_pr<R, EQ, 0>(bc, A, B, g, c, threads, s);
 }
 
-template <typename R, int EQ, int PR>
-cudaError_t persistent_launch_pr(int bc, R* A, R* B, const PersistentPlan& plan, const Coefs<R>& c,
-                                 uint32_t* flags, unsigned int* counter, int* status, int threads,
-                                 int blocks, cudaStream_t s)
-{
-    const size_t smem = sizeof(R) * smem_elems<EQ>(plan.n);
-    cudaError_t e = set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ, PR>, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
-    if (e != cudaSuccess) return e;
-    swept_persistent_kernel<R, EQ, PR><<<blocks, threads, smem, s>>>(A, B, plan, bc, c, flags, counter,
-                                                                      status);
-    return cudaGetLastError();
-}
-
-template <typename R, int EQ>
-cudaError_t persistent_launch_eq(int bc, R* A, R* B, const PersistentPlan& plan, const Coefs<R>& c,
-                                 uint32_t* flags, unsigned int* counter, int* status, int threads,
-                                 int blocks, cudaStream_t s)
-{
-    if constexpr (EQ != EULER) {
-        switch (reg_slots<R, EQ>(plan.n, threads)) {
-        case 2: return persistent_launch_pr<R, EQ, 2>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
-        case 4: return persistent_launch_pr<R, EQ, 4>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
-        case 8: return persistent_launch_pr<R, EQ, 8>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
-        case 16:
-            if constexpr (sizeof(R) == 4)
-                return persistent_launch_pr<R, EQ, 16>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
-            break;
-        default: break;
-        }
-    }
-    return persistent_launch_pr<R, EQ, 0>(bc, A, B, plan, c, flags, counter, status, threads, blocks, s);
-}
-
-template <typename R, int EQ, int PR>
-int persistent_bps_pr(int n, int threads)
-{
-    const size_t smem = sizeof(R) * smem_elems<EQ>(n);
-    if (set_smem<R, EQ>((const void*)swept_persistent_kernel<R, EQ, PR>, smem) != cudaSuccess) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_persistent_kernel<R, EQ, PR>, threads,
-                                                      smem) != cudaSuccess)
-        return 0;
-    return nb;
-}
-
-template <typename R, int EQ>
-int persistent_bps_eq(int n, int threads)
-{
-    if constexpr (EQ != EULER) {
-        switch (reg_slots<R, EQ>(n, threads)) {
-        case 2: return persistent_bps_pr<R, EQ, 2>(n, threads);
-        case 4: return persistent_bps_pr<R, EQ, 4>(n, threads);
-        case 8: return persistent_bps_pr<R, EQ, 8>(n, threads);
-        case 16:
-            if constexpr (sizeof(R) == 4) return persistent_bps_pr<R, EQ, 16>(n, threads);
-            break;
-        default: break;
-        }
-    }
-    return persistent_bps_pr<R, EQ, 0>(n, threads);
-}
-
 template <typename R, int EQ>
 cudaError_t register_launch_eq(R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
                                cudaStream_t s)
@@ -943,46 +818,11 @@ cudaError_t launch_swept_phase(int eq, int bc, R* A, R* B, const PhaseGeom& g, c
     }
 }
 
-template <typename R>
-cudaError_t launch_swept_persistent(int eq, int bc, R* A, R* B, const PersistentPlan& plan,
-                                    const Coefs<R>& c, uint32_t* flags, unsigned int* counter,
-                                    int* status, int threads, int blocks, cudaStream_t s)
-{
-    switch (eq) {
-    case HEAT:
-        return persistent_launch_eq<R, HEAT>(bc, A, B, plan, c, flags, counter, status, threads,
-                                             blocks, s);
-    case KS:
-        return persistent_launch_eq<R, KS>(bc, A, B, plan, c, flags, counter, status, threads,
-                                           blocks, s);
-    default:
-        return persistent_launch_eq<R, EULER>(bc, A, B, plan, c, flags, counter, status, threads,
-                                              blocks, s);
-    }
-}
-
-template <typename R>
-int swept_persistent_blocks_per_sm(int eq, int n, int threads)
-{
-    switch (eq) {
-    case HEAT: return persistent_bps_eq<R, HEAT>(n, threads);
-    case KS: return persistent_bps_eq<R, KS>(n, threads);
-    default: return persistent_bps_eq<R, EULER>(n, threads);
-    }
-}
 
 template cudaError_t launch_swept_phase<double>(int, int, double*, double*, const PhaseGeom&,
                                                 const Coefs<double>&, int, cudaStream_t);
 template cudaError_t launch_swept_phase<float>(int, int, float*, float*, const PhaseGeom&,
                                                const Coefs<float>&, int, cudaStream_t);
-template cudaError_t launch_swept_persistent<double>(int, int, double*, double*,
-                                                     const PersistentPlan&, const Coefs<double>&,
-                                                     uint32_t*, unsigned int*, int*, int, int,
-                                                     cudaStream_t);
-template cudaError_t launch_swept_persistent<float>(int, int, float*, float*,
-                                                    const PersistentPlan&, const Coefs<float>&,
-                                                    uint32_t*, unsigned int*, int*, int, int,
-                                                    cudaStream_t);
 template <typename R>
 cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
                                   int threads, cudaStream_t s)
@@ -1025,7 +865,5 @@ template cudaError_t launch_swept_register<float>(int, float*, float*, const Pha
                                                   const Coefs<float>&, int, cudaStream_t);
 template int swept_batch_blocks_per_sm<double>(int, bool, size_t, int);
 template int swept_batch_blocks_per_sm<float>(int, bool, size_t, int);
-template int swept_persistent_blocks_per_sm<double>(int, int, int);
-template int swept_persistent_blocks_per_sm<float>(int, int, int);
 
 }  // namespace swp
