@@ -33,7 +33,7 @@ from paper_1705_03162_gb300 import inputs as I  # noqa: E402
 
 DEFAULT_WORKLOAD = {
     "eq": "ks", "n_points": 1 << 20, "steps": 10_000, "dtype": "f64",
-    "points_per_block": 1024, "launch": "per_phase", "threads": 256,
+    "points_per_block": 512, "launch": "persistent", "threads": 256,
 }
 METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served solve latency"
 UNIT = "G point-updates/s"
@@ -55,7 +55,12 @@ NCU_TRAFFIC = {
     # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
     "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "10b4b7352ae120f5", "bytes_per_launch": 16783872},
+    # profiles/swept_batch_kernel_ks_n512.md: the whole 10^4-step solve in one dataflow launch,
+    # 1-pass capture of the bench's timed launch: 9.19 MB read + 3.00 MB written (ncu rounds to 10 kB)
+    "swept_batch_kernel<double,KS> n=512 threads=256": {"src": "a2dc297ca9fbbbb1", "bytes_per_launch": 12190000},
 }
+KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
+                    "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
 
 
 def _kernel_src_hash() -> str:
@@ -492,7 +497,8 @@ def run_gpu(args, wl):
     achieved = flops_per_launch / avg_launch_s / 1e12
     ops_rate = float(N) * steps * args.steps * KS_FP64_OPS_PER_UPDATE / t_swept / 1e12
     peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
-    key = f"swept_phase_kernel<{'float' if f32 else 'double'},KS> n={wl['points_per_block']} threads={wl['threads']}"
+    key = (f"{KERNEL_OF_LAUNCH[wl['launch']]}<{'float' if f32 else 'double'},KS> "
+           f"n={wl['points_per_block']} threads={wl['threads']}")
     traffic = None
     rec = NCU_TRAFFIC.get(key)
     if rec and rec.get("src") == _kernel_src_hash():
