@@ -569,8 +569,9 @@ def _time_solve(prob, u0d, steps, scheme, n=0, launch="per_phase", threads=0, re
 
 
 def run_sweep(steps: int = 2000):
-    """Swept (shared, best node width and launch), Register variant and classic
-    (CUDA graph) for heat and KS at N = 2^11..2^20, FP64: one JSON line each."""
+    """Swept (shared, best node width and launch: per-phase, graph or dataflow),
+    Register variant and classic (CUDA graph) for heat and KS at N = 2^11..2^20,
+    FP64: one JSON line each."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     for eq in ("ks", "heat"):
@@ -585,7 +586,7 @@ def run_sweep(steps: int = 2000):
                 for n in (64, 128, 256, 512, 1024):
                     if N % n or N // n < 2:
                         continue
-                    for launch in ("per_phase", "graph"):
+                    for launch in ("per_phase", "graph", "persistent"):
                         r = N * steps / _time_solve(p, u0d, steps, "swept", n, launch) / 1e9
                         if r > best:
                             best, cfg = r, {"points_per_block": n, "launch": launch}
