@@ -926,10 +926,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     bool reg = false;
     for (const auto& it : items)
         if (it.kind == BATCH_SWEPT && swept_reg_slots(it.p->desc.eq, it.s.n, threads, it.p->esize) > 0) reg = true;
-    int solo = items[0].p->desc.eq;
-    for (const auto& it : items)
-        if (it.kind != BATCH_SWEPT || it.p->desc.eq != solo) solo = -1;
-    const int bps = swept_batch_blocks_per_sm<R>(mode, reg, solo, smem, threads);
+    const int bps = swept_batch_blocks_per_sm<R>(mode, reg, smem, threads);
     if (bps <= 0) {
         if (graph) gnew.t.release();
         return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
@@ -940,7 +937,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     if (!graph) {
         e = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
-        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, reg, solo, dinsts, w, threads, (int)blocks, b->stream);
+        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     } else {
         // the uploads above are ordinary stream work; the graph holds the rest
@@ -957,7 +954,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
             cudaError_t e1 = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->capture_stream);
             if (e1 == cudaSuccess)
                 e1 = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->capture_stream);
-            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, reg, solo, dinsts, w, threads, (int)blocks, b->capture_stream);
+            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->capture_stream);
             e = cudaStreamEndCapture(b->capture_stream, &cg);
             if (e1 != cudaSuccess) e = e1;
         }

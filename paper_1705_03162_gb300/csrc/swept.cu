@@ -631,11 +631,8 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
     }
 }
 
-// MODE HEAT: heat and KS instances, swept or classic (chosen per item); MODE
-// EULER: Euler instances.  SOLO: every item is a swept node of equation MODE
-// (HEAT, KS or EULER), so the kernel carries only that code path (fewer
-// registers, more resident blocks).
-template <typename R, int MODE, bool REG, bool SOLO>
+// MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
+template <typename R, int MODE, bool REG>
 __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
                                                                                 BatchWork w)
 {
@@ -695,9 +692,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         }
         __syncthreads();
         if (abort_s) break;
-        if constexpr (SOLO) {
-            batch_item<R, MODE, REG>(in, k, p, smem_raw);
-        } else if constexpr (MODE == EULER) {
+        if constexpr (MODE == EULER) {
             if (in.kind == BATCH_SWEPT) batch_item<R, EULER, false>(in, k, p, smem_raw);
             else classic_item<R, EULER>(in, k, p, smem_raw);
         } else if (in.kind == BATCH_SWEPT) {
@@ -771,23 +766,23 @@ cudaError_t register_launch_eq(R* A, R* B, const PhaseGeom& g, const Coefs<R>& c
     return cudaGetLastError();
 }
 
-template <typename R, int MODE, bool REG, bool SOLO>
+template <typename R, int MODE, bool REG>
 cudaError_t batch_launch_mode(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
                               cudaStream_t s)
 {
-    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG, SOLO>, w.smem_bytes);
+    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, w.smem_bytes);
     if (e != cudaSuccess) return e;
-    swept_batch_kernel<R, MODE, REG, SOLO><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
+    swept_batch_kernel<R, MODE, REG><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
     return cudaGetLastError();
 }
 
-template <typename R, int MODE, bool REG, bool SOLO>
+template <typename R, int MODE, bool REG>
 int batch_bps_mode(size_t smem, int threads)
 {
-    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG, SOLO>, smem) != cudaSuccess) return 0;
+    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE, REG, SOLO>, threads,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE, REG>, threads, smem) !=
+        cudaSuccess)
         return 0;
     return nb;
 }
@@ -837,44 +832,20 @@ cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const 
 }
 
 template <typename R>
-cudaError_t launch_swept_batch(int mode, bool reg, int solo_eq, const BatchInst<R>* insts, const BatchWork& w,
-                               int threads, int blocks, cudaStream_t s)
+cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
+                               int blocks, cudaStream_t s)
 {
-    // register-blocked levels exist in FP32 only (swept_reg_slots)
-    constexpr bool kReg = sizeof(R) == 4;
-    if constexpr (kReg) {
-        if (reg && solo_eq == HEAT) return batch_launch_mode<R, HEAT, kReg, true>(insts, w, threads, blocks, s);
-        if (reg && solo_eq == KS) return batch_launch_mode<R, KS, kReg, true>(insts, w, threads, blocks, s);
-        if (reg && solo_eq < 0 && mode != EULER)
-            return batch_launch_mode<R, HEAT, kReg, false>(insts, w, threads, blocks, s);
-    }
-    switch (solo_eq) {
-    case HEAT: return batch_launch_mode<R, HEAT, false, true>(insts, w, threads, blocks, s);
-    case KS: return batch_launch_mode<R, KS, false, true>(insts, w, threads, blocks, s);
-    case EULER: return batch_launch_mode<R, EULER, false, true>(insts, w, threads, blocks, s);
-    default: break;
-    }
-    if (mode == EULER) return batch_launch_mode<R, EULER, false, false>(insts, w, threads, blocks, s);
-    return batch_launch_mode<R, HEAT, false, false>(insts, w, threads, blocks, s);
+    if (mode == EULER) return batch_launch_mode<R, EULER, false>(insts, w, threads, blocks, s);
+    if (reg) return batch_launch_mode<R, HEAT, true>(insts, w, threads, blocks, s);
+    return batch_launch_mode<R, HEAT, false>(insts, w, threads, blocks, s);
 }
 
 template <typename R>
-int swept_batch_blocks_per_sm(int mode, bool reg, int solo_eq, size_t smem_bytes, int threads)
+int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads)
 {
-    constexpr bool kReg = sizeof(R) == 4;
-    if constexpr (kReg) {
-        if (reg && solo_eq == HEAT) return batch_bps_mode<R, HEAT, kReg, true>(smem_bytes, threads);
-        if (reg && solo_eq == KS) return batch_bps_mode<R, KS, kReg, true>(smem_bytes, threads);
-        if (reg && solo_eq < 0 && mode != EULER) return batch_bps_mode<R, HEAT, kReg, false>(smem_bytes, threads);
-    }
-    switch (solo_eq) {
-    case HEAT: return batch_bps_mode<R, HEAT, false, true>(smem_bytes, threads);
-    case KS: return batch_bps_mode<R, KS, false, true>(smem_bytes, threads);
-    case EULER: return batch_bps_mode<R, EULER, false, true>(smem_bytes, threads);
-    default: break;
-    }
-    if (mode == EULER) return batch_bps_mode<R, EULER, false, false>(smem_bytes, threads);
-    return batch_bps_mode<R, HEAT, false, false>(smem_bytes, threads);
+    if (mode == EULER) return batch_bps_mode<R, EULER, false>(smem_bytes, threads);
+    if (reg) return batch_bps_mode<R, HEAT, true>(smem_bytes, threads);
+    return batch_bps_mode<R, HEAT, false>(smem_bytes, threads);
 }
 
 int swept_reg_slots(int eq, int n, int threads, int elem_bytes)
@@ -884,15 +855,15 @@ int swept_reg_slots(int eq, int n, int threads, int elem_bytes)
     return eq == HEAT ? reg_slots<double, HEAT>(n, threads) : reg_slots<double, KS>(n, threads);
 }
 
-template cudaError_t launch_swept_batch<double>(int, bool, int, const BatchInst<double>*, const BatchWork&,
-                                                int, int, cudaStream_t);
-template cudaError_t launch_swept_batch<float>(int, bool, int, const BatchInst<float>*, const BatchWork&,
-                                               int, int, cudaStream_t);
+template cudaError_t launch_swept_batch<double>(int, bool, const BatchInst<double>*, const BatchWork&, int,
+                                                int, cudaStream_t);
+template cudaError_t launch_swept_batch<float>(int, bool, const BatchInst<float>*, const BatchWork&, int,
+                                               int, cudaStream_t);
 template cudaError_t launch_swept_register<double>(int, double*, double*, const PhaseGeom&,
                                                    const Coefs<double>&, int, cudaStream_t);
 template cudaError_t launch_swept_register<float>(int, float*, float*, const PhaseGeom&,
                                                   const Coefs<float>&, int, cudaStream_t);
-template int swept_batch_blocks_per_sm<double>(int, bool, int, size_t, int);
-template int swept_batch_blocks_per_sm<float>(int, bool, int, size_t, int);
+template int swept_batch_blocks_per_sm<double>(int, bool, size_t, int);
+template int swept_batch_blocks_per_sm<float>(int, bool, size_t, int);
 
 }  // namespace swp
