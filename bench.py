@@ -49,25 +49,33 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
-# a hash of the kernel sources it was taken on; reported as null once the
-# sources change.
+# a hash of the kernel sources it was taken on (code only: comments and blank
+# lines do not count); reported as null once the code changes.
 NCU_TRAFFIC = {
     # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
-    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "10b4b7352ae120f5", "bytes_per_launch": 16783872},
+    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "5e80a285e7a01b44", "bytes_per_launch": 16783872},
     # profiles/swept_batch_kernel_ks_n512.md: the whole 10^4-step solve in one dataflow launch,
     # 1-pass capture of the bench's timed launch: 9.19 MB read + 3.00 MB written (ncu rounds to 10 kB)
-    "swept_batch_kernel<double,KS> n=512 threads=256": {"src": "a2dc297ca9fbbbb1", "bytes_per_launch": 12190000},
+    "swept_batch_kernel<double,KS> n=512 threads=256": {"src": "b59575fd0a82ca7f", "bytes_per_launch": 12190000},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
 
 
+def _code_only(text: str) -> str:
+    """Source without comments and blank lines (a comment edit does not change a kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def _kernel_src_hash() -> str:
     h = hashlib.sha256()
     for f in ("swept.cu", "scheme.cuh", "launch.h"):
-        with open(os.path.join(ROOT, "paper_1705_03162_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1705_03162_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_phase_kernel(R
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form: one launch for the whole advance.
+// Flags between the items of a persistent (dataflow) launch.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p)
 {
@@ -505,7 +505,9 @@ __global__ void __launch_bounds__(256) swept_register_kernel(R* A, R* B, PhaseGe
 }
 
 // ---------------------------------------------------------------------------
-// Batched persistent form (many independent problems of one equation).
+// Persistent dataflow form: one launch runs every phase of one or many
+// problems (a single problem's SWP_LAUNCH_PERSISTENT advance is a batch of
+// one).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int ld_relaxed(const int* p)
 {
