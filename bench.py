@@ -367,11 +367,11 @@ def other_configs() -> dict:
     from paper_1705_03162_gb300 import swept as S
     out = {}
     for name, eq, N, steps, n in (("heat N=1024 r=0.25 4096 steps n=64", "heat", 1024, 4096, 64),
-                                  ("Sod Euler N=2^20 4096 steps n=512", "euler", 1 << 20, 4096, 512)):
+                                  ("Sod Euler N=2^20 4096 steps n=512 dataflow", "euler", 1 << 20, 4096, 512)):
         spec, u0 = _spec_ic(eq, N)
         u0d = torch.from_numpy(u0).cuda()
         with S.Problem(spec, u0d) as p:
-            ts = _time_solve(p, u0d, steps, "swept", n, "graph" if eq == "heat" else "per_phase")
+            ts = _time_solve(p, u0d, steps, "swept", n, "graph" if eq == "heat" else "persistent")
             tc = _time_solve(p, u0d, steps, "classic", launch="graph")
         out[name] = {"swept": N * steps / ts / 1e9, "classic_graph": N * steps / tc / 1e9,
                      "unit": UNIT, "swept_speedup": tc / ts}
@@ -605,8 +605,8 @@ def run_sweep(steps: int = 2000):
 
 def run_sod(exps, steps: int, widths=None, threads=None):
     """Sod shock tube (dt/dx = 0.2, Dirichlet ends), FP64, fixed step count:
-    swept at each node width and block size against classic on a stream and as
-    a CUDA graph; one JSON line per N."""
+    swept at each node width, block size and launch (per-phase, dataflow)
+    against classic on a stream and as a CUDA graph; one JSON line per N."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     for e in exps:
@@ -621,8 +621,9 @@ def run_sod(exps, steps: int, widths=None, threads=None):
                 if N % n or N // n < 2:
                     continue
                 for t in threads or (128, 256):
-                    r = N * steps / _time_solve(p, u0d, steps, "swept", n, "per_phase", t) / 1e9
-                    runs.append({"points_per_block": n, "threads": t, "swept": r})
+                    for launch in ("per_phase", "persistent"):
+                        r = N * steps / _time_solve(p, u0d, steps, "swept", n, launch, t) / 1e9
+                        runs.append({"points_per_block": n, "threads": t, "launch": launch, "swept": r})
         best = max(runs, key=lambda x: x["swept"])
         print(json.dumps({"sod": f"N=2^{e}", "timesteps": steps, "dtype": "f64", "unit": UNIT,
                           "classic": classic, "classic_graph": classic_graph, "swept_best": best,
