@@ -681,7 +681,8 @@ def main():
         ap.error("--warmup must be >= 3")
     wl = dict(DEFAULT_WORKLOAD, launch=args.launch, dtype=args.dtype)
     if args.dtype == "f32":
-        wl["threads"] = 128   # 8 slots per thread: the register-blocked FP32 levels
+        # per-phase launches of the register-blocked FP32 levels (8 slots per thread)
+        wl.update(points_per_block=1024, launch="per_phase", threads=128)
     for key, val in (("points_per_block", args.points_per_block), ("threads", args.threads),
                      ("steps", args.timesteps)):
         if val is not None:

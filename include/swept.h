@@ -88,8 +88,8 @@ typedef struct {
 
 /* How swp_advance_ex runs the swept scheme. */
 typedef enum {
-    SWP_LAUNCH_AUTO = 0,        /* library choice: PERSISTENT from N = 2^17,
-                                   PER_PHASE below */
+    SWP_LAUNCH_AUTO = 0,        /* library choice: PERSISTENT for FP64 from
+                                   N = 2^17, PER_PHASE otherwise */
     SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
                                    nodes synchronise at kernel boundaries */
     SWP_LAUNCH_PERSISTENT = 2,  /* one dataflow kernel for the whole advance

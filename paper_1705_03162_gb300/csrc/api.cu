@@ -454,11 +454,12 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         if (s.top & 1) p->cur = 1 - p->cur;
         return SWP_OK;
     }
-    // AUTO: the dataflow (persistent) launch from N = 2^17 up, where it
-    // measured faster than per-phase launches; per-phase launches below
+    // AUTO: in FP64 the dataflow (persistent) launch from N = 2^17 up, where
+    // it measured faster than per-phase launches; per-phase launches below,
+    // and in FP32, where the per-phase kernels' register-blocked levels win
     const int launch = o.launch != SWP_LAUNCH_AUTO ? o.launch
-                                                   : (p->N >= ((int64_t)1 << 17) ? SWP_LAUNCH_PERSISTENT
-                                                                                 : SWP_LAUNCH_PER_PHASE);
+                       : (p->N >= ((int64_t)1 << 17) && p->desc.dtype == SWP_F64) ? SWP_LAUNCH_PERSISTENT
+                                                                                  : SWP_LAUNCH_PER_PHASE;
     int n = o.points_per_block;
     if (n == 0) {
         n = default_width(p, launch == SWP_LAUNCH_PERSISTENT);
