@@ -103,8 +103,9 @@ typedef enum {
     SWP_LAUNCH_REGISTER = 4     /* the paper's Register variant (Section 5.1):
                                    one warp per node of 32 points, levels in
                                    registers, neighbours by warp shuffle; one
-                                   kernel per phase; periodic heat and KS only
-                                   (points_per_block 32 or 0) */
+                                   kernel per phase, replayed as a CUDA graph
+                                   like SWP_LAUNCH_GRAPH; periodic heat and KS
+                                   only (points_per_block 32 or 0) */
 } swp_launch;
 
 typedef struct {
