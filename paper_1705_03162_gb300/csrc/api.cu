@@ -307,12 +307,14 @@ swp_status run_swept_register(swp_problem* p, const SweptPlan& s, int threads)
 }
 
 template <typename R>
-swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads)
+swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads, int64_t p_lo = 0,
+                            int64_t p_hi = -1)
 {
     R* A = (R*)p->rows[p->cur];
     R* B = (R*)p->rows[1 - p->cur];
     const Coefs<R>& c = coefs_of<R>(p);
-    for (int64_t ph = 0; ph < s.n_phases; ++ph) {
+    if (p_hi < 0) p_hi = s.n_phases;
+    for (int64_t ph = p_lo; ph < p_hi; ++ph) {
         PhaseGeom g;
         g.N = p->N;
         g.n = s.n;
@@ -1202,6 +1204,25 @@ swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int coun
         groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
     }
     return launch_groups(b, groups, threads, false);
+}
+
+swp_status advance_phases(swp_problem* p, int n, int64_t steps, int64_t p_lo, int64_t p_hi)
+{
+    if (!p) return fail(SWP_EINVAL, "problem is NULL");
+    swp_status st = check_width(p, n);
+    if (st != SWP_OK) return st;
+    const SweptPlan s = plan_swept(p, steps, n);
+    if (p_lo < 0 || p_hi > s.n_phases || p_lo > p_hi)
+        return fail(SWP_EINVAL, "phases [%lld, %lld) outside the plan", (long long)p_lo, (long long)p_hi);
+    if (p_lo == p_hi) return SWP_OK;
+    // the same per-phase kernels and block size as swp_advance's per-phase launch
+    const int threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
+    const int thr = p->desc.dtype == SWP_F32 ? std::max(64, std::min(256, n / 8)) / 32 * 32 : threads;
+    st = p->desc.dtype == SWP_F64 ? run_swept_phases<double>(p, s, thr, p_lo, p_hi)
+                                  : run_swept_phases<float>(p, s, thr, p_lo, p_hi);
+    if (st != SWP_OK) return st;
+    if (p_hi == s.n_phases && (s.top & 1)) p->cur = 1 - p->cur;
+    return SWP_OK;
 }
 
 }  // namespace swp

@@ -119,5 +119,7 @@ struct PhaseRange {
 int swept_width(const swp_problem* p);   // the tuned or default node width
 int64_t swept_phase_count(const swp_problem* p, int64_t steps, int n);
 swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads);
+// The same for one problem, as per-phase launches on its own stream.
+swp_status advance_phases(swp_problem* p, int n, int64_t steps, int64_t p_lo, int64_t p_hi);
 
 }  // namespace swp

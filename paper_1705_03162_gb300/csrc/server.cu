@@ -12,8 +12,10 @@
 //    active request an equal share of a target round time as credit
 //    (estimated FP64 work per point-update of its equation) and runs as many
 //    of its next phases as its credit pays for (deficit round robin), all in
-//    one batched launch per group; requests that arrive meanwhile join the
-//    next round, so new and in-flight work overlap on the device;
+//    one batched launch per group (a round of one request below 2^17 points,
+//    or in FP32, runs as that request's per-phase launches, as swp_advance
+//    would run it alone); requests that arrive meanwhile join the next round,
+//    so new and in-flight work overlap on the device;
 //  - retirement: finished requests are copied back to host memory, their
 //    device memory is freed, and waiters are woken.
 // A request's phases are those of one swept advance of its whole step count,
@@ -181,9 +183,24 @@ swp_status swp_server::round()
         ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i]});
     }
     const int64_t l0 = swp_batch_kernel_launches(batch);
-    swp_status st = swp::batch_advance_phases(batch, ranges.data(), (int)ranges.size(), cfg.threads);
-    if (st == SWP_OK) st = swp_batch_synchronize(batch);
-    launches += swp_batch_kernel_launches(batch) - l0;
+    swp_status st = SWP_OK;
+    bool solo_phases = false;   // one request, of a size where per-phase launches beat the batched kernel
+    if (ranges.size() == 1)
+        for (auto& rq : active)
+            if (rq->prob == ranges[0].p)
+                solo_phases = rq->desc.n_points < ((int64_t)1 << 17) || rq->desc.dtype == SWP_F32;
+    if (solo_phases) {
+        // as swp_advance would run it alone (SWP_LAUNCH_AUTO)
+        const swp::PhaseRange& r = ranges[0];
+        const int64_t k0 = swp_kernel_launches(r.p);
+        st = swp::advance_phases(r.p, r.n, r.steps, r.p_lo, r.p_hi);
+        if (st == SWP_OK) st = swp_synchronize(r.p);
+        launches += swp_kernel_launches(r.p) - k0;
+    } else {
+        st = swp::batch_advance_phases(batch, ranges.data(), (int)ranges.size(), cfg.threads);
+        if (st == SWP_OK) st = swp_batch_synchronize(batch);
+        launches += swp_batch_kernel_launches(batch) - l0;
+    }
     rounds++;
     for (size_t i = 0; i < active.size(); ++i) {
         Request& r = *active[i];
