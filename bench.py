@@ -33,7 +33,7 @@ from paper_1705_03162_gb300 import inputs as I  # noqa: E402
 
 DEFAULT_WORKLOAD = {
     "eq": "ks", "n_points": 1 << 20, "steps": 10_000, "dtype": "f64",
-    "points_per_block": 512, "launch": "persistent", "threads": 256,
+    "points_per_block": 1024, "launch": "persistent", "threads": 256,
 }
 METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served solve latency"
 UNIT = "G point-updates/s"

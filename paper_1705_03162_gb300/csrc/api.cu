@@ -161,17 +161,17 @@ swp_status check_width(const swp_problem* p, int n)
 }
 
 // Default node width, from the widths measured fastest on GB300 for single
-// problems: about N / 1024 points for heat and KS (at least 64 and 128, at
-// most 1024; at most 512 in the persistent dataflow launch) and N / 256 for
-// Euler (64 to 512); the nearest width that divides N, is a multiple of
-// 4 rad and fits shared memory.
+// problems: about N / 1024 points for heat and KS (N / 512 in the persistent
+// dataflow launch; at least 64 and 128, at most 1024) and N / 256 for Euler
+// (64 to 512); the nearest width that divides N, is a multiple of 4 rad and
+// fits shared memory.
 int default_width(const swp_problem* p, bool dataflow = false)
 {
     const int step = 4 * p->rad;
     const bool euler = p->desc.eq == SWP_EULER;
     const int lo = (p->desc.eq == SWP_HEAT || euler) ? 64 : 128;
-    const int cap = (euler || dataflow) ? 512 : 1024;
-    int64_t target = p->N / (euler ? 256 : 1024);
+    const int cap = euler ? 512 : 1024;
+    int64_t target = p->N / (euler ? 256 : (dataflow ? 512 : 1024));
     if (target < lo) target = lo;
     if (target > cap) target = cap;
     if (target > p->N / 2) target = p->N / 2;
@@ -480,6 +480,8 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     if (threads == 0) {
         if (p->desc.dtype == SWP_F32)   // about 8 points per thread (register-blocked levels)
             threads = std::max(64, std::min(256, n / 8)) / 32 * 32;
+        else if (launch == SWP_LAUNCH_PERSISTENT)   // measured: 256 from 256-point nodes up
+            threads = n >= 256 ? 256 : (n >= 128 ? 128 : 64);
         else
             threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
     }
@@ -811,7 +813,8 @@ double level_cost(int eq) { return eq == SWP_HEAT ? 3.0 : (eq == SWP_KS ? 7.0 : 
 // settings (the single-problem persistent launch and its test hook).
 template <typename R>
 swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mode, int threads, bool graph,
-                       int* status = nullptr, uint32_t wait_offset = 0, uint64_t wait_limit = 0)
+                       int* status = nullptr, uint32_t wait_offset = 0, uint64_t wait_limit = 0,
+                       int max_blocks_per_sm = 0)
 {
     std::vector<int64_t> key;
     if (graph) {
@@ -936,7 +939,8 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     bool reg = false;
     for (const auto& it : items)
         if (it.kind == BATCH_SWEPT && swept_reg_slots(it.p->desc.eq, it.s.n, threads, it.p->esize) > 0) reg = true;
-    const int bps = swept_batch_blocks_per_sm<R>(mode, reg, smem, threads);
+    int bps = swept_batch_blocks_per_sm<R>(mode, reg, smem, threads);
+    if (max_blocks_per_sm > 0 && bps > max_blocks_per_sm) bps = max_blocks_per_sm;
     if (bps <= 0) {
         if (graph) gnew.t.release();
         return fail(SWP_EINVAL, "batch kernel does not fit (%zu bytes of shared memory, threads=%d)", smem, threads);
@@ -1014,10 +1018,16 @@ swp_status persistent_via_batch(swp_problem* p, const SweptPlan& s, int threads)
     items[0].flip = false;   // the caller moves the state's row
     const int mode = p->desc.eq == SWP_EULER ? SWP_EULER : SWP_HEAT;
     const uint32_t withhold = p->inject_withheld_flags ? (1u << 30) : 0u;
+    // at most 768 threads (24 warps) per SM: with fewer nodes in flight each
+    // finishes sooner and the phase chain advances faster (KS 2^20, 1024-point
+    // nodes: 40.0 against 36.8 G upd/s with 5 blocks of 256 per SM)
+    const int max_bps = std::max(1, 768 / threads);
     const int64_t l0 = p->launches;
     swp_status st = p->desc.dtype == SWP_F64
-                        ? batch_group<double>(p->batch, items, mode, threads, false, p->status, withhold, p->wait_limit_ns)
-                        : batch_group<float>(p->batch, items, mode, threads, false, p->status, withhold, p->wait_limit_ns);
+                        ? batch_group<double>(p->batch, items, mode, threads, false, p->status, withhold,
+                                              p->wait_limit_ns, max_bps)
+                        : batch_group<float>(p->batch, items, mode, threads, false, p->status, withhold,
+                                             p->wait_limit_ns, max_bps);
     if (st == SWP_OK && p->launches != l0 + 1) p->launches = l0 + 1;
     return st;
 }
