@@ -55,9 +55,9 @@ NCU_TRAFFIC = {
     # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
     # full-diamond launch (16.78 MB + 0), cold caches
     "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "5e80a285e7a01b44", "bytes_per_launch": 16783872},
-    # profiles/swept_batch_kernel_ks_n512.md: the whole 10^4-step solve in one dataflow launch,
-    # 1-pass capture of the bench's timed launch: 9.19 MB read + 3.00 MB written (ncu rounds to 10 kB)
-    "swept_batch_kernel<double,KS> n=512 threads=256": {"src": "b59575fd0a82ca7f", "bytes_per_launch": 12190000},
+    # profiles/swept_batch_kernel_ks_n1024.md: the whole 10^4-step solve in one dataflow launch,
+    # 1-pass capture of the bench's timed launch: 9.04 MB read + 2.78 MB written (ncu rounds to 10 kB)
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "3d7312d1b92eb997", "bytes_per_launch": 11820000},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
