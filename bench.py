@@ -172,6 +172,22 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle baseline (test infrastructure, timed as it stands)
 # ---------------------------------------------------------------------------
+def _host_cpu() -> dict:
+    """Core count and CPU model of the host the CPU baseline ran on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model, "arch": platform.machine()}
+
+
 def cpu_oracle_rate(wl: dict, budget_s: float = 12.0) -> dict:
     import oracle as O
     spec = I.ks_spec(wl["n_points"])
@@ -185,6 +201,7 @@ def cpu_oracle_rate(wl: dict, budget_s: float = 12.0) -> dict:
     O.classic(prob, u, steps)
     el = time.perf_counter() - t0
     return {"value": spec.n_points * steps / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": _host_cpu(),
             "sample": f"KS N=2^20 FP64 classic oracle, {steps} timesteps from the initial state "
                       f"(of the workload's {wl['steps']}), single thread, {el:.1f} s"}
 
@@ -214,7 +231,8 @@ def run_reference(args, wl):
         "data": "synthetic",
         "config": {"workload": "KS N=2^20 FP64 10^4 steps (dx=0.5, dt=0.005)", "n_points": wl["n_points"],
                    "timesteps": wl["steps"], "sample_timesteps": sample_steps},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": _host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
