@@ -36,6 +36,7 @@ DEFAULT_WORKLOAD = {
     "points_per_block": 1024, "launch": "persistent", "threads": 256,
 }
 METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served solve latency"
+WORKLOAD = "KS N=2^20 {} 10^4 steps (dx=0.5, dt=0.005, u0=cos(x/16)(1+sin(x/16)))"
 UNIT = "G point-updates/s"
 
 # Floating-point operations of one KS point-update (two RK2 stages of seven
@@ -229,8 +230,9 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "KS N=2^20 FP64 10^4 steps (dx=0.5, dt=0.005)", "n_points": wl["n_points"],
-                   "timesteps": wl["steps"], "sample_timesteps": sample_steps},
+        "config": {"workload": WORKLOAD.format("FP64"), "n_points": wl["n_points"],
+                   "timesteps": wl["steps"], "sample_timesteps": sample_steps, "scheme": "classic (CPU oracle)",
+                   "parallelism": "one host thread"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                          "host": _host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -545,8 +547,7 @@ def run_gpu(args, wl):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_swept / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"], "data": "synthetic",
-        "config": {"workload": f"KS N=2^20 {'FP32' if f32 else 'FP64'} 10^4 steps (dx=0.5, dt=0.005, "
-                               "u0=cos(x/16)(1+sin(x/16)))",
+        "config": {"workload": WORKLOAD.format("FP32" if f32 else "FP64"),
                    "n_points": N, "timesteps": steps, "scheme": "swept",
                    "points_per_block": wl["points_per_block"], "launch": wl["launch"],
                    "parallelism": f"replicas x{world}",
