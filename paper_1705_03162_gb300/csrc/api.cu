@@ -800,6 +800,8 @@ SweptPlan plan_classic(const swp_problem* p, int64_t steps, int m)
 swp_status check_chunk(const swp_problem* p, int m)
 {
     if (m < 4 || m > p->N) return fail(SWP_EINVAL, "classic chunk width %d must be in [4, n_points]", m);
+    if ((p->N + m - 1) / m >= ((int64_t)1 << 30))
+        return fail(SWP_EINVAL, "classic chunk width %d gives 2^30 or more chunks", m);
     if (batch_classic_smem_bytes(p->desc.eq, m, p->esize) > max_smem(p->device))
         return fail(SWP_EINVAL, "classic chunk width %d does not fit shared memory", m);
     return SWP_OK;

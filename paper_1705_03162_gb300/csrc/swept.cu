@@ -581,8 +581,12 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
 {
     constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
     const int64_t N = in.N;
-    const int64_t x0 = (int64_t)k * N / in.K;
-    const int cnt = (int)((int64_t)(k + 1) * N / in.K - x0);
+    // chunk k is [floor(kN/K), floor((k+1)N/K)), with kN split so that it
+    // cannot overflow (N < 2^35, K < 2^30)
+    const int64_t q = N / in.K, rem = N % in.K;
+    const int64_t x0 = (int64_t)k * q + (int64_t)k * rem / in.K;
+    const int64_t x1 = (int64_t)(k + 1) * q + (int64_t)(k + 1) * rem / in.K;
+    const int cnt = (int)(x1 - x0);
     const int W = cnt + 2 * RAD;
     R* sm = reinterpret_cast<R*>(smem_raw);   // [NV][W]: the chunk and its halo
     const bool even = (p & 1) == 0;
