@@ -233,6 +233,19 @@ def test_large_size_swept_equals_classic(eq):
     assert np.all(np.isfinite(a))
 
 
+@pytest.mark.parametrize("eq,N,steps", [("ks", 1 << 26, 300), ("heat", 1 << 27, 1100)])
+def test_large_fp64_dataflow_equals_classic(eq, N, steps):
+    """FP64 grids of 0.5-1 GB per row through the default launch (the dataflow
+    kernel from 2^17 points): bit-identical to classic, with several full
+    half-cycles and a remainder."""
+    spec = spec_for(eq, "periodic", N)
+    u0 = I.initial_state(spec)
+    a = _gpu(spec, u0, steps, "f64", "classic")
+    b = _gpu(spec, u0, steps, "f64", "swept", 0, "auto")
+    assert np.array_equal(a, b)
+    assert np.all(np.isfinite(a))
+
+
 def test_invalid_node_width_rejected():
     spec = spec_for("ks", "periodic", 1000)
     with S.Problem(spec, state_for(spec)) as p:
