@@ -111,6 +111,8 @@ def _load():
         lib.orc_euler_interface_f64.restype = ctypes.c_int
         lib.orc_euler_reconstruct_f64.argtypes = [vp, ctypes.c_double, vp, vp]
         lib.orc_euler_reconstruct_f64.restype = ctypes.c_int
+        lib.orc_swept_geometry.argtypes = [i32, i64, i64, vp]
+        lib.orc_swept_geometry.restype = ctypes.c_int
         lib.orc_euler_pressure_f64.argtypes = [vp, ctypes.c_double]
         lib.orc_euler_pressure_f64.restype = ctypes.c_double
         _lib = lib
@@ -145,6 +147,15 @@ def swept(problem: OracleProblem, state: np.ndarray, steps: int, n: int) -> np.n
     p = problem._c()
     _check(_load().orc_swept(ctypes.byref(p), dt, state.ctypes.data, int(steps), int(n)), "swept")
     return state
+
+
+def swept_geometry(eq: int, n: int, steps: int) -> dict:
+    """The swept plan the oracle runs for nodes of ``n`` points (Sections
+    4.2-4.3): levels per half-cycle H, slots per working-array row W, full
+    half-cycles Q, remaining levels r, kernels, and timesteps per triangle."""
+    out = np.zeros(6, dtype=np.int64)
+    _check(_load().orc_swept_geometry(int(eq), int(n), int(steps), out.ctypes.data), "geometry")
+    return dict(zip(("H", "W", "Q", "r", "kernels", "triangle_steps"), (int(x) for x in out)))
 
 
 def euler_interface(q4: np.ndarray, gamma: float = 1.4) -> np.ndarray:

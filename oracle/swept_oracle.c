@@ -58,6 +58,32 @@ typedef struct {
     double right[3];
 } orc_problem;
 
+/* Geometry of the swept plan (Sections 4.2-4.3) for nodes of n points and a
+ * stencil of radius rad (sub sub-timesteps per timestep): H sub-timestep
+ * levels per half-cycle, so an upright triangle of H - 1 levels above its base
+ * advances H / sub timesteps; each node works in two rows of W = n + 2 rad
+ * slots; `steps` timesteps take Q full half-cycles plus r remaining levels,
+ * in `kernels` kernels (triangle, diamonds, closing triangle). */
+typedef struct {
+    int64_t H, W, Q, r, kernels, triangle_steps;
+} orc_geometry;
+
+static int swept_geometry(int rad, int sub, int64_t n, int64_t steps, orc_geometry* g)
+{
+    if (n <= 0 || n % (2 * rad) || steps < 0) return ORC_EINVAL;
+    g->H = n / (2 * rad);
+    /* H even keeps the level parity of every kernel's base level even, so the
+     * predictor / final alternation and the two rows line up in every node */
+    if (g->H & 1) return ORC_EINVAL;
+    g->W = n + 2 * rad;
+    int64_t T = steps * sub;
+    g->Q = T / g->H;
+    g->r = T % g->H;
+    g->kernels = T == 0 ? 0 : (g->r > 0 ? g->Q + 2 : g->Q + 1);
+    g->triangle_steps = g->H / sub;
+    return ORC_OK;
+}
+
 /* FP64 instantiation */
 #define REAL double
 #define SFX(x) x##_f64
@@ -122,6 +148,23 @@ int orc_swept(const orc_problem* pb, int32_t dtype, void* state, int64_t steps, 
     if (dtype == ORC_F64) return swept_f64(pb, (double*)state, steps, n);
     if (dtype == ORC_F32) return swept_f32(pb, (float*)state, steps, n);
     return ORC_EINVAL;
+}
+
+/* The swept geometry the oracle runs, for the pins against the paper's
+ * figures: out = (H, W, Q, r, kernels, timesteps per triangle). */
+int orc_swept_geometry(int32_t eq, int64_t n, int64_t steps, int64_t* out)
+{
+    if (!out || eq < ORC_HEAT || eq > ORC_EULER) return ORC_EINVAL;
+    orc_geometry g;
+    int e = swept_geometry(eq == ORC_HEAT ? 1 : 2, eq == ORC_HEAT ? 1 : 2, n, steps, &g);
+    if (e) return e;
+    out[0] = g.H;
+    out[1] = g.W;
+    out[2] = g.Q;
+    out[3] = g.r;
+    out[4] = g.kernels;
+    out[5] = g.triangle_steps;
+    return ORC_OK;
 }
 
 /* Pieces of the Euler scheme, exposed for the pins that check them on

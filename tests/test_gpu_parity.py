@@ -246,6 +246,20 @@ def test_large_fp64_dataflow_equals_classic(eq, N, steps):
     assert np.all(np.isfinite(a))
 
 
+@pytest.mark.parametrize("eq,n,steps", [("heat", 64, 4096), ("heat", 64, 100), ("ks", 128, 333), ("euler", 64, 50)])
+def test_phase_count_matches_oracle_geometry(eq, n, steps):
+    """The per-phase launch issues exactly the oracle's kernels: upright
+    triangle, diamonds, closing triangle (and a truncated one for a
+    remainder)."""
+    bc = "dirichlet" if eq == "euler" else "periodic"
+    spec = spec_for(eq, bc, 16 * n)
+    g = O.swept_geometry({"heat": O.HEAT, "ks": O.KS, "euler": O.EULER}[eq], n, steps)
+    with S.Problem(spec, state_for(spec)) as p:
+        k0 = p.kernel_launches()
+        p.advance(steps, "swept", n, "per_phase")
+        assert p.kernel_launches() - k0 == g["kernels"]
+
+
 def test_invalid_node_width_rejected():
     spec = spec_for("ks", "periodic", 1000)
     with S.Problem(spec, state_for(spec)) as p:

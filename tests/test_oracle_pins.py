@@ -407,3 +407,35 @@ def test_swept_rejects_bad_node_width():
         O.swept(oprob(spec48), I.initial_state(spec48), 4, 12)   # H = n / 4 = 3 odd
     with pytest.raises(O.OracleError):
         O.classic(O.OracleProblem(O.KS, O.REFLECTIVE, 64, 0.5, 0.005), u, 1)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64, 128, 1024])
+def test_swept_geometry_first_order_triangle_is_n_over_2(n):
+    """Section 4.2: a first-order (heat) node of n points advances n/2
+    timesteps per triangle, in a working array of two rows of n + k - 1 slots
+    (stencil width k = 3)."""
+    g = O.swept_geometry(O.HEAT, n, 1000)
+    assert g["triangle_steps"] == n // 2
+    assert g["W"] == n + 3 - 1
+
+
+@pytest.mark.parametrize("eq", [O.KS, O.EULER])
+@pytest.mark.parametrize("n", [32, 64, 256, 1024])
+def test_swept_geometry_second_order_triangle_is_n_over_8(eq, n):
+    """Sections 4.2 and 6: a second-order scheme (two sub-steps of a 5-point
+    stencil) advances n/8 timesteps per triangle; the paper's example is
+    n = 32 -> 4 timesteps.  Working array rows of n + 5 - 1 slots."""
+    g = O.swept_geometry(eq, n, 1000)
+    assert g["triangle_steps"] == n // 8
+    assert g["W"] == n + 5 - 1
+    if n == 32:
+        assert g["triangle_steps"] == 4
+
+
+def test_swept_geometry_rejects_odd_half_cycles():
+    """H = n / (2 rad) must be even (the rows' level parity) and n a multiple
+    of 2 rad."""
+    assert O.swept_geometry(O.KS, 24, 10)["H"] == 6
+    for eq, n in ((O.KS, 20), (O.HEAT, 30), (O.KS, 18)):
+        with pytest.raises(O.OracleError):
+            O.swept_geometry(eq, n, 10)
