@@ -116,6 +116,9 @@ typedef struct {
     int32_t threads;           /* threads per block (0 = auto; multiple of 32) */
 } swp_advance_opts;
 
+/* A problem handle is used by one host thread at a time (calls on different
+ * problems may run concurrently; the server's problems belong to its own
+ * scheduler thread). */
 typedef struct swp_problem swp_problem;
 
 /* Create a problem on the current CUDA device and copy its initial state.
@@ -183,7 +186,9 @@ size_t swp_memory_in_use(void);
  *                     ceil(N / m) chunks of at most m points.
  * Each problem's result is bit-identical to swp_advance with the same scheme
  * (and, swept, the same node width).  The table costs 12 bytes of device
- * memory per (problem, phase) task.  The paper has no batched form. */
+ * memory per (problem, phase) task; this workspace is not counted against
+ * swp_set_memory_budget.  A batch, like its problems, is used by one host
+ * thread at a time.  The paper has no batched form. */
 typedef struct swp_batch swp_batch;
 
 /* A batch runs its work on cuda_stream (NULL = legacy default stream); every
