@@ -97,3 +97,34 @@ def test_missing_library_raises(tmp_path, monkeypatch):
     monkeypatch.setattr(S, "_lib", None)
     with pytest.raises(S.LibraryError):
         S.load_library(str(tmp_path / "nope.so"))
+
+
+def test_tuned_choice_defaults_to_swept(lib):
+    """With nothing measured for a key, SWP_SCHEME_AUTO means swept at the
+    default width (no device needed to ask)."""
+    d = S.make_desc(I.ks_spec(3 * 1024 + 512))
+    sc, n = ctypes.c_int32(-1), ctypes.c_int32(-1)
+    assert lib.swp_tuned(ctypes.byref(d), ctypes.byref(sc), ctypes.byref(n)) == S.OK
+    assert (sc.value, n.value) == (S.SWEPT, 0)
+    w = ctypes.c_int32(-1)
+    assert lib.swp_tuned_width(ctypes.byref(d), ctypes.byref(w)) == S.OK and w.value == 0
+
+
+def test_tuning_and_batch_entry_points_validate_on_the_host(lib):
+    d = S.make_desc(I.ks_spec(1024))
+    d.eq = 9
+    sc, n = ctypes.c_int32(0), ctypes.c_int32(0)
+    buf = (ctypes.c_double * 1024)()
+    assert lib.swp_autotune(ctypes.byref(d), buf, 8, 10, ctypes.byref(sc), ctypes.byref(n)) == S.EINVAL
+    d = S.make_desc(I.ks_spec(1024))
+    assert lib.swp_autotune(ctypes.byref(d), None, 8, 10, ctypes.byref(sc), ctypes.byref(n)) == S.EINVAL
+    assert lib.swp_autotune(ctypes.byref(d), buf, 0, 10, ctypes.byref(sc), ctypes.byref(n)) == S.EINVAL
+    assert lib.swp_batch_advance_ex(None, None, None, 0, None, None, 0, 0) == S.EINVAL
+    assert lib.swp_batch_kernel_launches(None) == -1
+    assert lib.swp_batch_destroy(None) == S.OK
+
+
+def test_scheme_enum_matches_header():
+    text = open(os.path.join(ROOT, "include", "swept.h")).read()
+    assert "SWP_CLASSIC = 0" in text and "SWP_SWEPT = 1" in text and "SWP_SCHEME_AUTO = 2" in text
+    assert (S.CLASSIC, S.SWEPT, S.SCHEME_AUTO) == (0, 1, 2)
