@@ -71,22 +71,88 @@ __device__ __forceinline__ R wall_fetch(const R* row, int W, int q, int d, int v
     return row[v * W + q + d];
 }
 
+// 16-byte vectors of the working precision.
+template <typename R> struct Vec16;
+template <> struct Vec16<double> {
+    using T = double2;
+    static constexpr int W = 2;
+};
+template <> struct Vec16<float> {
+    using T = float4;
+    static constexpr int W = 4;
+};
+
+template <typename R, bool CG>
+__device__ __forceinline__ typename Vec16<R>::T load_vec(const R* p)
+{
+    using T = typename Vec16<R>::T;
+    return CG ? __ldcg(reinterpret_cast<const T*>(p)) : *reinterpret_cast<const T*>(p);
+}
+
+template <typename R, bool CG>
+__device__ __forceinline__ void store_vec(R* p, const typename Vec16<R>::T& v)
+{
+    using T = typename Vec16<R>::T;
+    if (CG) __stcg(reinterpret_cast<T*>(p), v);
+    else *reinterpret_cast<T*>(p) = v;
+}
+
+// Move `count` consecutive points of a global row (period N) starting at
+// global point g into shared memory at s (IN) or back (OUT).  The range is
+// split where it wraps; inside each piece the block moves 16-byte vectors
+// from the first 16-byte-aligned address on, and single values before and
+// after.
+template <typename R, bool CG, bool IN>
+__device__ __forceinline__ void row_copy(R* row, int64_t N, int64_t g, int count, R* s)
+{
+    constexpr int VW = Vec16<R>::W;
+    g = wrap(g, N);
+    for (int done = 0; done < count;) {
+        const int len = (int)min((int64_t)(count - done), N - g);
+        R* gp = row + g;
+        R* sp = s + done;
+        const int head = min(len, (int)(((16 - (reinterpret_cast<uintptr_t>(gp) & 15)) & 15) / sizeof(R)));
+        const int body = (len - head) / VW;
+        const int tail = len - head - body * VW;
+        for (int t = threadIdx.x; t < head + tail; t += blockDim.x) {
+            const int q = t < head ? t : head + body * VW + (t - head);
+            if (IN) sp[q] = CG ? __ldcg(gp + q) : gp[q];
+            else if (CG) __stcg(gp + q, sp[q]);
+            else gp[q] = sp[q];
+        }
+        for (int i = threadIdx.x; i < body; i += blockDim.x) {
+            const int q = head + i * VW;
+            if (IN) {
+                const typename Vec16<R>::T v = load_vec<R, CG>(gp + q);
+                const R* e = reinterpret_cast<const R*>(&v);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) sp[q + k] = e[k];
+            } else {
+                typename Vec16<R>::T v;
+                R* e = reinterpret_cast<R*>(&v);
+#pragma unroll
+                for (int k = 0; k < VW; ++k) e[k] = sp[q + k];
+                store_vec<R, CG>(gp + q, v);
+            }
+        }
+        done += len;
+        g = 0;
+    }
+}
+
 // Load the node window of rows A / B (global, [NV][N]) into shared memory.
-// Row 0 (A) occupies slots [rad, rad + n); row 1 (B) all W slots.
+// Row 0 (A) occupies slots [rad, rad + n); row 1 (B) all W slots.  Coalesced
+// 16-byte vector loads (row_copy).
 template <typename R, int EQ, bool CG>
 __device__ __forceinline__ void window_load(const R* A, const R* B, R* row0, R* row1, int n,
                                             int64_t g0, int64_t N, bool need_b)
 {
     constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
     const int W = window_width(n, RAD);
-    for (int s = threadIdx.x; s < W; s += blockDim.x) {
-        const int64_t g = wrap(g0 + s, N);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            if (s >= RAD && s < RAD + n)
-                row0[v * W + s] = CG ? __ldcg(A + v * N + g) : A[v * N + g];
-            if (need_b) row1[v * W + s] = CG ? __ldcg(B + v * N + g) : B[v * N + g];
-        }
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+        row_copy<R, CG, true>(const_cast<R*>(A) + v * N, N, g0 + RAD, n, row0 + v * W + RAD);
+        if (need_b) row_copy<R, CG, true>(const_cast<R*>(B) + v * N, N, g0, W, row1 + v * W);
     }
 }
 
@@ -98,19 +164,10 @@ __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R*
 {
     constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
     const int W = window_width(n, RAD);
-    for (int s = threadIdx.x; s < W; s += blockDim.x) {
-        const int64_t g = wrap(g0 + s, N);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            if (s >= RAD && s < RAD + n) {
-                if (CG) __stcg(A + v * N + g, row0[v * W + s]);
-                else A[v * N + g] = row0[v * W + s];
-            }
-            if (s >= 2 * RAD && s < n) {
-                if (CG) __stcg(B + v * N + g, row1[v * W + s]);
-                else B[v * N + g] = row1[v * W + s];
-            }
-        }
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+        row_copy<R, CG, false>(A + v * N, N, g0 + RAD, n, const_cast<R*>(row0) + v * W + RAD);
+        row_copy<R, CG, false>(B + v * N, N, g0 + 2 * RAD, n - 2 * RAD, const_cast<R*>(row1) + v * W + 2 * RAD);
     }
 }
 
