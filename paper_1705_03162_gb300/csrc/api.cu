@@ -23,6 +23,7 @@ using namespace swp;
 
 struct swp_problem {
     swp_desc desc;
+    uint64_t id = 0;   // unique per created problem (keys of cached batch graphs)
     int nv = 1, rad = 1, sub = 1, esize = 8;
     int64_t N = 0;
     void* rows[2] = {nullptr, nullptr};   // level rows / classic ping-pong, [nv][N] each
@@ -56,6 +57,7 @@ namespace {
 thread_local std::string g_last_error;
 std::atomic<size_t> g_in_use{0};
 std::atomic<size_t> g_budget{0};
+std::atomic<uint64_t> g_next_id{1};
 
 swp_status fail(swp_status s, const char* fmt, ...)
 {
@@ -402,13 +404,12 @@ swp_status run_graph(swp_problem* p, int64_t steps, int scheme, int n, int threa
     p->stream = user;
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(p->capture_stream, &graph);
-    if (st != SWP_OK) {
+    if (st != SWP_OK || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         p->cur = g.cur_before;
         p->launches = launches0;
-        return st;
+        return st != SWP_OK ? st : cuda_fail(e, "end capture");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "end capture");
     if (scheme != SWP_CLASSIC && (s->top & 1)) p->cur = 1 - p->cur;
     g.cur_after = p->cur;
     g.kernels = p->launches - launches0;
@@ -556,6 +557,7 @@ swp_status swp_create(const swp_desc* desc, const void* u0, int u0_on_device, vo
         return fail(SWP_ENOMEM, "host allocation failed");
     }
     p->desc = *desc;
+    p->id = g_next_id.fetch_add(1);
     p->nv = nv_of(desc->eq);
     p->rad = radius_of(desc->eq);
     p->sub = desc->eq == SWP_HEAT ? 1 : 2;
@@ -824,7 +826,8 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         key.push_back(mode);
         key.push_back(threads);
         for (const auto& it : items) {
-            key.push_back((int64_t)(intptr_t)it.p);
+            // the id, not the address: a new problem may reuse a destroyed one's
+            key.push_back((int64_t)it.p->id);
             key.push_back(it.p->cur);
             key.push_back(it.kind);
             key.push_back(it.s.n);

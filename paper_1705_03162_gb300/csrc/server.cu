@@ -183,6 +183,8 @@ swp_status swp_server::round()
         ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i]});
     }
     const int64_t l0 = swp_batch_kernel_launches(batch);
+    int64_t round_launches = 0;
+    double round_updates = 0.0;
     swp_status st = SWP_OK;
     bool solo_phases = false;   // one request, of a size where per-phase launches beat the batched kernel
     if (ranges.size() == 1)
@@ -195,13 +197,12 @@ swp_status swp_server::round()
         const int64_t k0 = swp_kernel_launches(r.p);
         st = swp::advance_phases(r.p, r.n, r.steps, r.p_lo, r.p_hi);
         if (st == SWP_OK) st = swp_synchronize(r.p);
-        launches += swp_kernel_launches(r.p) - k0;
+        round_launches = swp_kernel_launches(r.p) - k0;
     } else {
         st = swp::batch_advance_phases(batch, ranges.data(), (int)ranges.size(), cfg.threads);
         if (st == SWP_OK) st = swp_batch_synchronize(batch);
-        launches += swp_batch_kernel_launches(batch) - l0;
+        round_launches = swp_batch_kernel_launches(batch) - l0;
     }
-    rounds++;
     for (size_t i = 0; i < active.size(); ++i) {
         Request& r = *active[i];
         if (st != SWP_OK) {
@@ -212,9 +213,14 @@ swp_status swp_server::round()
         r.phase_next += take[i];
         if (r.phase_next >= r.n_phases) {
             r.steps_done = r.steps_total;
-            point_updates += (double)r.steps_total * (double)r.desc.n_points;
+            round_updates += (double)r.steps_total * (double)r.desc.n_points;
         }
     }
+    // the statistics are read by other threads under mu
+    std::lock_guard<std::mutex> lock(mu);
+    rounds++;
+    launches += round_launches;
+    point_updates += round_updates;
     return st;
 }
 

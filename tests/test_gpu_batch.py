@@ -223,3 +223,24 @@ def test_autotune_scheme_and_auto_advances():
     for p in ps:
         assert np.array_equal(p.read(), ref)
         p.close()
+
+
+def test_batch_graph_cache_after_problems_replaced():
+    """Problems destroyed and new ones created between graph advances (the
+    host may reuse their addresses): each advance runs on the live problems'
+    rows, never on a cached graph of destroyed ones."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    spec = I.ks_spec(2048)
+    u0 = state_for(spec)
+    ref = u0.copy()
+    O.classic(oprob(spec), ref, 9)
+    with S.Batch(stream) as b:
+        for _ in range(3):
+            ps = [S.Problem(spec, u0, stream=stream) for _ in range(2)]
+            b.advance_ex(ps, [9, 9], ["swept", "swept"], [256, 256], launch="graph")
+            b.synchronize()
+            for p in ps:
+                assert np.array_equal(p.read(), ref)
+                p.close()
+        assert b.kernel_launches() == 3
