@@ -249,12 +249,14 @@ def _spec_ic(eq: str, N: int, dtype=np.float64):
     return spec, I.initial_state(spec, dtype)
 
 
-def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
+def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), width: int = 0,
+                threads: int = 0) -> dict:
     """4096 independent heat + KS instances, N log-uniform 2^10..2^16, steps
     U(10^3, 10^4), one persistent launch per precision replayed from a CUDA
     graph, scheme (swept or classic) and width autotuned per (equation,
-    power-of-two N) bucket; against advancing a sample of the same instances
-    one by one."""
+    power-of-two N) bucket (or every instance swept at node width `width`,
+    halved until it divides N); against advancing a sample of the same
+    instances one by one."""
     import math
     import torch
     from paper_1705_03162_gb300 import swept as S
@@ -264,14 +266,15 @@ def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
         N = max(1024, int(round(2 ** rng.uniform(10, 16) / 128)) * 128)
         cases.append(("heat" if i % 2 == 0 else "ks", N, int(rng.integers(1000, 10001))))
     out = {"instances": count, "workload": "heat+KS, N log-uniform 2^10..2^16, steps U(1e3,1e4)"}
-    for dtype in ("f64", "f32"):
+    for dtype in dtypes:
         npdt = np.float64 if dtype == "f64" else np.float32
         t0 = time.perf_counter()
         tuned = {}
         for eq in ("heat", "ks"):
             for e in range(10, 17):
                 spec, u0 = _spec_ic(eq, 2 ** e, npdt)
-                tuned[(eq, e)] = S.autotune(spec, u0, count=256, steps=128, dtype=dtype)
+                tuned[(eq, e)] = ("swept", width) if width else S.autotune(spec, u0, count=256, steps=128,
+                                                                            dtype=dtype)
         tune_s = time.perf_counter() - t0
         stream = torch.cuda.Stream()
         probs, schemes, widths = [], [], []
@@ -293,17 +296,17 @@ def run_batched(count: int = 4096, seed: int = 20170509) -> dict:
             # advance ends in its other row alternates between two); the timed
             # third advance replays the first graph
             for _ in range(2):
-                bt.advance_ex(probs, steps, schemes, widths, launch="graph")
+                bt.advance_ex(probs, steps, schemes, widths, threads=threads, launch="graph")
             bt.synchronize()
             l0 = bt.kernel_launches()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            bt.advance_ex(probs, steps, schemes, widths, launch="graph")
+            bt.advance_ex(probs, steps, schemes, widths, threads=threads, launch="graph")
             ev1.record(stream)
             bt.synchronize()
             ms = ev0.elapsed_time(ev1)
             launches = bt.kernel_launches() - l0
-        sample = range(32)
+        sample = range(min(32, count))
         su = float(sum(cases[i][1] * cases[i][2] for i in sample))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -707,6 +710,10 @@ def main():
                     help="print Sod swept-vs-classic lines for N = 2^LOG2N (default 11 14 17 20) instead; "
                          "--timesteps defaults to 4096 here, and --points-per-block / --threads, when given, "
                          "fix the swept configuration")
+    ap.add_argument("--batched", type=int, metavar="COUNT",
+                    help="print the batched heat+KS line for COUNT instances in the --dtype precision instead; "
+                         "--points-per-block, when given, replaces the autotuned widths, and --threads sets "
+                         "the batch's block size")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the served, batched and FP32-error measurements")
     args = ap.parse_args()
@@ -722,6 +729,13 @@ def main():
             wl[key] = val
     if args.impl == "reference":
         run_reference(args, wl)
+    elif args.batched is not None:
+        from paper_1705_03162_gb300 import swept as S
+        S.load_library()
+        if args.batched < 1:
+            ap.error("--batched needs COUNT >= 1")
+        print(json.dumps({"batched": run_batched(args.batched, dtypes=(args.dtype,),
+                                                 width=args.points_per_block or 0, threads=args.threads or 0)}))
     elif args.sod is not None:
         from paper_1705_03162_gb300 import swept as S
         S.load_library()

@@ -142,7 +142,12 @@ swp_status swp_write(swp_problem* p, const void* src, size_t src_bytes, int src_
  * the state is complete afterwards (Section 4.2: output only at closing
  * triangles); a final partial half-cycle is closed exactly.
  * Asynchronous on the problem's stream.  SWP_ETIMEOUT reports a persistent
- * launch whose bounded neighbour wait gave up (the state is then invalid). */
+ * launch whose bounded neighbour wait gave up (the state is then invalid).
+ * Each such wait gives up after 2 s of device global time, or after the
+ * number of nanoseconds (1 to 10^12) in the environment variable
+ * SWP_WAIT_LIMIT_NS, read once per process: raise it to run persistent
+ * launches under a tool that pauses or replays kernels (a profiler's
+ * multi-pass replay). */
 swp_status swp_advance(swp_problem* p, int64_t n_steps, int32_t scheme, int32_t points_per_block);
 swp_status swp_advance_ex(swp_problem* p, int64_t n_steps, const swp_advance_opts* opts);
 
@@ -199,7 +204,8 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out);
  * points_per_block: per-problem node widths, or NULL / 0 entries for the
  * tuned width of swp_autotune_width (else the default rule).  threads: block
  * size (0 = 128 for FP64 and 32 for FP32; Euler at most 256).  Problems must be distinct.  Asynchronous;
- * SWP_ETIMEOUT surfaces at swp_batch_synchronize. */
+ * SWP_ETIMEOUT surfaces at swp_batch_synchronize (wait bound as for
+ * swp_advance's persistent launch, SWP_WAIT_LIMIT_NS included). */
 swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps,
                              int32_t count, const int32_t* points_per_block, int32_t threads);
 

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -73,6 +74,22 @@ swp_status fail(swp_status s, const char* fmt, ...)
 swp_status cuda_fail(cudaError_t e, const char* what)
 {
     return fail(SWP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Bound of one neighbour wait of a persistent launch: 2 s, or the value of
+// SWP_WAIT_LIMIT_NS (nanoseconds, 1 .. 10^12; read once), for tools that
+// pause or replay kernels (a profiler's multi-pass replay stretches waits).
+uint64_t default_wait_limit_ns()
+{
+    static const uint64_t v = [] {
+        const char* s = std::getenv("SWP_WAIT_LIMIT_NS");
+        if (!s || !*s) return (uint64_t)2000000000ull;
+        char* end = nullptr;
+        const unsigned long long x = std::strtoull(s, &end, 10);
+        if (*end != '\0' || x == 0 || x > 1000000000000ull) return (uint64_t)2000000000ull;
+        return (uint64_t)x;
+    }();
+    return v;
 }
 
 int radius_of(int eq) { return eq == SWP_HEAT ? 1 : 2; }
@@ -558,6 +575,7 @@ swp_status swp_create(const swp_desc* desc, const void* u0, int u0_on_device, vo
     }
     p->desc = *desc;
     p->id = g_next_id.fetch_add(1);
+    p->wait_limit_ns = default_wait_limit_ns();
     p->nv = nv_of(desc->eq);
     p->rad = radius_of(desc->eq);
     p->sub = desc->eq == SWP_HEAT ? 1 : 2;
@@ -1251,6 +1269,7 @@ swp_status swp_batch_create(void* cuda_stream, swp_batch** out)
     swp_batch* b = new (std::nothrow) swp_batch();
     if (!b) return fail(SWP_ENOMEM, "host allocation failed");
     b->stream = (cudaStream_t)cuda_stream;
+    b->wait_limit_ns = default_wait_limit_ns();
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e != cudaSuccess) {
