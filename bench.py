@@ -57,8 +57,8 @@ NCU_TRAFFIC = {
     # full-diamond launch (16.78 MB + 0), cold caches
     "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "5e80a285e7a01b44", "bytes_per_launch": 16783872},
     # profiles/swept_batch_kernel_ks_n1024.md: the whole 10^4-step solve in one dataflow launch,
-    # 1-pass capture of the bench's timed launch: 9.05 MB read + 2.88 MB written (ncu rounds to 10 kB)
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "1ea57e6c4dc8d00d", "bytes_per_launch": 11930000},
+    # 1-pass capture of the bench's timed launch: 8.98 MB read + 2.67 MB written (ncu rounds to 10 kB)
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "62b75750d8ebfd2b", "bytes_per_launch": 11650000},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}

@@ -204,8 +204,10 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n,
                 dst[q] = heat_point(tm, src[q], tp, c.fo);
             }
         } else if constexpr (EQ == KS) {
-            // KS problems are periodic: the window is already wrapped.
-            const R a1 = c.a1[stage], a4 = c.a4[stage], beta = c.beta[stage], gam = c.gam[stage];
+            // KS problems are periodic: the window is already wrapped.  (The
+            // stage picks by value: c may be a copy in registers.)
+            const R a1 = stage ? c.a1[1] : c.a1[0], a4 = stage ? c.a4[1] : c.a4[0];
+            const R beta = stage ? c.beta[1] : c.beta[0], gam = stage ? c.gam[1] : c.gam[0];
             for (int t = threadIdx.x; t < cnt; t += T) {
                 const int q = lo + t;
                 const R base = stage == 0 ? src[q] : row0[q];
@@ -590,17 +592,31 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
     const int64_t g0 = xc - n / 2 - RAD;
     window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
+    // heat / KS: the point-update coefficients in registers for all levels,
+    // rather than re-read from the instance table after every level barrier
+    Coefs<R> cr{};
+    if constexpr (EQ != EULER) {
+        cr.fo = in.c.fo;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            cr.a1[s] = in.c.a1[s];
+            cr.a4[s] = in.c.a4[s];
+            cr.beta[s] = in.c.beta[s];
+            cr.gam[s] = in.c.gam[s];
+        }
+    }
+    const Coefs<R>& c = EQ != EULER ? cr : in.c;
     __syncthreads();
     bool done = false;
     if constexpr (REG && EQ != EULER) {
         done = !node_near_wall(in.bc, k, in.K);
         if (done) switch (n / (int)blockDim.x) {
-        case 2: tile_levels_reg<R, EQ, 2>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
-        case 4: tile_levels_reg<R, EQ, 4>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
-        case 8: tile_levels_reg<R, EQ, 8>(row0, row1, P, n, H, j_lo, j_hi, in.c); break;
+        case 2: tile_levels_reg<R, EQ, 2>(row0, row1, P, n, H, j_lo, j_hi, c); break;
+        case 4: tile_levels_reg<R, EQ, 4>(row0, row1, P, n, H, j_lo, j_hi, c); break;
+        case 8: tile_levels_reg<R, EQ, 8>(row0, row1, P, n, H, j_lo, j_hi, c); break;
         case 16:
             if constexpr (sizeof(R) == 4) {
-                tile_levels_reg<R, EQ, 16>(row0, row1, P, n, H, j_lo, j_hi, in.c);
+                tile_levels_reg<R, EQ, 16>(row0, row1, P, n, H, j_lo, j_hi, c);
                 break;
             }
             done = false;
@@ -610,7 +626,7 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     }
     if (!done)
         run_levels<R, EQ, 0>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
-                             in.bc, in.c);
+                             in.bc, c);
     window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
 }
 
