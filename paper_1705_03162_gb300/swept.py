@@ -298,6 +298,17 @@ def swept_noalloc(spec: ProblemSpec, state, steps: int, n: int = 0, threads: int
     return state
 
 
+def _per_problem(name: str, values, count: int, ctype, convert=int):
+    """ctypes array of one value per problem (None stays None); a list of
+    another length is an error, not a silent zero fill."""
+    if values is None:
+        return None
+    values = list(values)
+    if len(values) != count:
+        raise ValueError(f"{name} has {len(values)} entries for {count} problems")
+    return (ctype * count)(*[convert(x) for x in values])
+
+
 class Batch:
     """Batched advance: many problems (created with this batch's stream)
     advanced together in one persistent launch per (equation, dtype) group."""
@@ -311,8 +322,8 @@ class Batch:
     def advance(self, problems, steps, n=None, threads: int = 0):
         count = len(problems)
         hs = (ctypes.c_void_p * count)(*[p._h.value for p in problems])
-        st = (ctypes.c_int64 * count)(*[int(x) for x in steps])
-        nn = None if n is None else (ctypes.c_int32 * count)(*[int(x) for x in n])
+        st = _per_problem("steps", steps, count, ctypes.c_int64)
+        nn = _per_problem("n", n, count, ctypes.c_int32)
         _check(self._lib.swp_batch_advance(self._h, hs, st, count, nn, int(threads)), "batch_advance")
 
     def advance_ex(self, problems, steps, schemes=None, n=None, threads: int = 0, launch: str = "auto"):
@@ -320,9 +331,9 @@ class Batch:
         and width (node or chunk); launch "auto" or "graph"."""
         count = len(problems)
         hs = (ctypes.c_void_p * count)(*[p._h.value for p in problems])
-        st = (ctypes.c_int64 * count)(*[int(x) for x in steps])
-        sc = None if schemes is None else (ctypes.c_int32 * count)(*[_SCHEME[x] for x in schemes])
-        nn = None if n is None else (ctypes.c_int32 * count)(*[int(x) for x in n])
+        st = _per_problem("steps", steps, count, ctypes.c_int64)
+        sc = _per_problem("schemes", schemes, count, ctypes.c_int32, lambda x: _SCHEME[x])
+        nn = _per_problem("n", n, count, ctypes.c_int32)
         _check(self._lib.swp_batch_advance_ex(self._h, hs, st, count, sc, nn, int(threads), _LAUNCH[launch]),
                "batch_advance_ex")
 

@@ -128,3 +128,17 @@ def test_scheme_enum_matches_header():
     text = open(os.path.join(ROOT, "include", "swept.h")).read()
     assert "SWP_CLASSIC = 0" in text and "SWP_SWEPT = 1" in text and "SWP_SCHEME_AUTO = 2" in text
     assert (S.CLASSIC, S.SWEPT, S.SCHEME_AUTO) == (0, 1, 2)
+
+
+def test_batch_lists_must_match_problem_count():
+    """A per-problem list shorter or longer than the problem list is an error
+    in the binding (ctypes would zero-fill a short one: a silent 0-step
+    advance)."""
+    arr = S._per_problem("steps", [5, 6, 7], 3, ctypes.c_int64)
+    assert list(arr) == [5, 6, 7]
+    assert S._per_problem("n", None, 3, ctypes.c_int32) is None
+    sc = S._per_problem("schemes", ["swept", "classic"], 2, ctypes.c_int32, lambda x: S._SCHEME[x])
+    assert list(sc) == [S._SCHEME["swept"], S._SCHEME["classic"]]
+    for bad in ([5, 6], [5, 6, 7, 8]):
+        with pytest.raises(ValueError):
+            S._per_problem("steps", bad, 3, ctypes.c_int64)
