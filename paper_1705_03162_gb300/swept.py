@@ -185,6 +185,15 @@ def _buffer(x):
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _host_state(spec: ProblemSpec, u0, dtype: str) -> np.ndarray:
+    """u0 as a C-contiguous host array of the problem's dtype, checked to hold
+    nv * N values: the library reads exactly that many from the pointer."""
+    a = np.ascontiguousarray(u0, dtype=np.float64 if dtype == "f64" else np.float32)
+    if a.size != spec.nv * spec.n_points:
+        raise ValueError(f"u0 has {a.size} values, expected {spec.nv} x {spec.n_points}")
+    return a
+
+
 def required_bytes(spec: ProblemSpec, dtype: str = "f64") -> int:
     lib = load_library()
     out = ctypes.c_size_t(0)
@@ -366,7 +375,7 @@ def autotune_width(spec: ProblemSpec, u0: np.ndarray, count: int = 16, steps: in
     """Time ``count`` copies of the problem in one batch for each node width and
     keep the fastest for later batches of this (equation, dtype, N)."""
     lib = load_library()
-    u0 = np.ascontiguousarray(u0)
+    u0 = _host_state(spec, u0, dtype)
     out = ctypes.c_int32(0)
     _check(lib.swp_autotune_width(ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data, int(count),
                                   int(steps), ctypes.byref(out)), "autotune_width")
@@ -385,7 +394,7 @@ def autotune(spec: ProblemSpec, u0: np.ndarray, count: int = 16, steps: int = 20
     copies; keep the faster for this (equation, dtype, N).  Returns
     (scheme name, width)."""
     lib = load_library()
-    u0 = np.ascontiguousarray(u0)
+    u0 = _host_state(spec, u0, dtype)
     sc, n = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(lib.swp_autotune(ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data, int(count), int(steps),
                             ctypes.byref(sc), ctypes.byref(n)), "autotune")
@@ -414,7 +423,7 @@ class Server:
         self._shapes = {}
 
     def submit(self, spec: ProblemSpec, u0: np.ndarray, steps: int, dtype: str = "f64") -> int:
-        u0 = np.ascontiguousarray(u0)
+        u0 = _host_state(spec, u0, dtype)
         rid = ctypes.c_int64(0)
         st = self._lib.swp_server_submit(self._h, ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data,
                                          int(steps), ctypes.byref(rid))

@@ -142,3 +142,18 @@ def test_batch_lists_must_match_problem_count():
     for bad in ([5, 6], [5, 6, 7, 8]):
         with pytest.raises(ValueError):
             S._per_problem("steps", bad, 3, ctypes.c_int64)
+
+
+def test_host_state_checks_size_and_dtype():
+    """Host initial states given by pointer (server submit, autotuners) are
+    checked and converted in the binding: the library reads nv * N values."""
+    import numpy as np
+    spec = I.sod_spec(64)
+    a = S._host_state(spec, np.zeros((3, 64)), "f64")
+    assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == 192
+    b = S._host_state(I.ks_spec(64), np.zeros((1, 64)), "f32")
+    assert b.dtype == np.float32
+    with pytest.raises(ValueError):
+        S._host_state(spec, np.zeros((1, 64)), "f64")
+    with pytest.raises(ValueError):
+        S._host_state(I.ks_spec(64), np.zeros(63), "f64")
