@@ -1239,6 +1239,8 @@ swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int coun
     return launch_groups(b, groups, threads, false);
 }
 
+swp_status set_error(swp_status s, const char* msg) { return fail(s, "%s", msg); }
+
 swp_status advance_phases(swp_problem* p, int n, int64_t steps, int64_t p_lo, int64_t p_hi)
 {
     if (!p) return fail(SWP_EINVAL, "problem is NULL");

@@ -38,6 +38,11 @@
 #include "../../include/swept.h"
 #include "launch.h"
 
+namespace swp {
+// Record `msg` as this thread's swp_last_error and return s (api.cu).
+swp_status set_error(swp_status s, const char* msg);
+}  // namespace swp
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -280,16 +285,17 @@ extern "C" {
 
 swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, swp_server** out)
 {
-    if (!cfg || !out) return SWP_EINVAL;
+    if (!cfg || !out) return swp::set_error(SWP_EINVAL, "server config or out is NULL");
     *out = nullptr;
-    if (cfg->max_active <= 0 || !(cfg->round_target_ms > 0) || cfg->threads < 0) return SWP_EINVAL;
+    if (cfg->max_active <= 0 || !(cfg->round_target_ms > 0) || cfg->threads < 0)
+        return swp::set_error(SWP_EINVAL, "server config: max_active and round_target_ms must be > 0, threads >= 0");
     swp_server* s = new (std::nothrow) swp_server();
-    if (!s) return SWP_ENOMEM;
+    if (!s) return swp::set_error(SWP_ENOMEM, "host allocation failed");
     s->cfg = *cfg;
     s->stream = (cudaStream_t)cuda_stream;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
-        return SWP_EDEVICE;
+        return swp::set_error(SWP_EDEVICE, "no usable CUDA device");
     }
     swp_status st = swp_batch_create(cuda_stream, &s->batch);
     if (st != SWP_OK) {
@@ -304,7 +310,8 @@ swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, sw
 swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0_host, int64_t n_steps,
                              int64_t* request_id)
 {
-    if (!s || !desc || !u0_host || !request_id || n_steps < 1) return SWP_EINVAL;
+    if (!s || !desc || !u0_host || !request_id || n_steps < 1)
+        return swp::set_error(SWP_EINVAL, "server, desc, u0_host or request_id is NULL, or n_steps < 1");
     size_t req = 0;
     swp_status st = swp_required_bytes(desc, &req);   // validates the description
     if (st != SWP_OK) return st;
@@ -316,7 +323,7 @@ swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(s->mu);
-        if (s->stop) return SWP_EINVAL;
+        if (s->stop) return swp::set_error(SWP_EINVAL, "the server is shutting down");
         r->id = s->next_id++;
         if (!s->any_submit) {
             s->any_submit = true;
@@ -332,30 +339,30 @@ swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0
 
 swp_status swp_server_poll(swp_server* s, int64_t id, int32_t* done)
 {
-    if (!s || !done) return SWP_EINVAL;
+    if (!s || !done) return swp::set_error(SWP_EINVAL, "server or done is NULL");
     std::lock_guard<std::mutex> lock(s->mu);
     auto it = s->all.find(id);
-    if (it == s->all.end()) return SWP_EINVAL;
+    if (it == s->all.end()) return swp::set_error(SWP_EINVAL, "unknown request id");
     *done = it->second->state == 2 ? 1 : 0;
     return SWP_OK;
 }
 
 swp_status swp_server_wait(swp_server* s, int64_t id, void* dst_host, size_t dst_bytes, double* latency_s)
 {
-    if (!s) return SWP_EINVAL;
+    if (!s) return swp::set_error(SWP_EINVAL, "server is NULL");
     std::shared_ptr<Request> r;
     {
         std::unique_lock<std::mutex> lock(s->mu);
         auto it = s->all.find(id);
-        if (it == s->all.end()) return SWP_EINVAL;
+        if (it == s->all.end()) return swp::set_error(SWP_EINVAL, "unknown request id (or already waited for)");
         r = it->second;
         s->cv_done.wait(lock, [&] { return r->state == 2; });
         s->all.erase(id);
     }
     if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
-    if (r->status != SWP_OK) return r->status;
+    if (r->status != SWP_OK) return swp::set_error(r->status, "the request failed (its status is returned)");
     if (dst_host) {
-        if (dst_bytes < r->result.size()) return SWP_EINVAL;
+        if (dst_bytes < r->result.size()) return swp::set_error(SWP_EINVAL, "dst_bytes smaller than the state");
         std::memcpy(dst_host, r->result.data(), r->result.size());
     }
     return SWP_OK;
@@ -363,7 +370,7 @@ swp_status swp_server_wait(swp_server* s, int64_t id, void* dst_host, size_t dst
 
 swp_status swp_server_stats(swp_server* s, swp_server_statistics* out)
 {
-    if (!s || !out) return SWP_EINVAL;
+    if (!s || !out) return swp::set_error(SWP_EINVAL, "server or out is NULL");
     std::lock_guard<std::mutex> lock(s->mu);
     out->completed = s->completed;
     out->rounds = s->rounds;

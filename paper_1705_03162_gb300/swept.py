@@ -417,18 +417,15 @@ class Server:
         self._h = ctypes.c_void_p(0)
         cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(threads), float(round_target_ms))
         handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
-        st = self._lib.swp_server_create(ctypes.byref(cfg), ctypes.c_void_p(handle), ctypes.byref(self._h))
-        if st != OK:
-            raise SweptError(st, "server_create", "invalid configuration or device")
+        _check(self._lib.swp_server_create(ctypes.byref(cfg), ctypes.c_void_p(handle), ctypes.byref(self._h)),
+               "server_create")
         self._shapes = {}
 
     def submit(self, spec: ProblemSpec, u0: np.ndarray, steps: int, dtype: str = "f64") -> int:
         u0 = _host_state(spec, u0, dtype)
         rid = ctypes.c_int64(0)
-        st = self._lib.swp_server_submit(self._h, ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data,
-                                         int(steps), ctypes.byref(rid))
-        if st != OK:
-            raise SweptError(st, "server_submit", load_library().swp_last_error().decode())
+        _check(self._lib.swp_server_submit(self._h, ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data,
+                                           int(steps), ctypes.byref(rid)), "server_submit")
         self._shapes[rid.value] = (u0.shape, u0.dtype)
         return rid.value
 
@@ -442,9 +439,8 @@ class Server:
         shape, dt = self._shapes.pop(rid)
         out = np.empty(shape, dtype=dt)
         lat = ctypes.c_double(0.0)
-        st = self._lib.swp_server_wait(self._h, int(rid), out.ctypes.data, out.nbytes, ctypes.byref(lat))
-        if st != OK:
-            raise SweptError(st, "server_wait", f"request {rid} failed")
+        _check(self._lib.swp_server_wait(self._h, int(rid), out.ctypes.data, out.nbytes, ctypes.byref(lat)),
+               f"server_wait (request {rid})")
         return out, lat.value
 
     def stats(self) -> dict:

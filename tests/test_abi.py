@@ -157,3 +157,23 @@ def test_host_state_checks_size_and_dtype():
         S._host_state(spec, np.zeros((1, 64)), "f64")
     with pytest.raises(ValueError):
         S._host_state(I.ks_spec(64), np.zeros(63), "f64")
+
+
+def test_server_argument_errors_set_last_error(lib):
+    """The serving entry points reject bad arguments on the host, before any
+    device call, and say why through swp_last_error."""
+    out = ctypes.c_void_p(0)
+    cfg = S.ServerConfig(0, 0, 0, 5.0)   # max_active 0
+    assert lib.swp_server_create(ctypes.byref(cfg), None, ctypes.byref(out)) == S.EINVAL
+    assert b"max_active" in lib.swp_last_error()
+    cfg = S.ServerConfig(0, 4, 0, 0.0)   # round_target_ms 0
+    assert lib.swp_server_create(ctypes.byref(cfg), None, ctypes.byref(out)) == S.EINVAL
+    assert lib.swp_server_create(None, None, ctypes.byref(out)) == S.EINVAL
+    assert b"NULL" in lib.swp_last_error()
+    rid = ctypes.c_int64(0)
+    assert lib.swp_server_submit(None, None, None, 10, ctypes.byref(rid)) == S.EINVAL
+    done = ctypes.c_int32(0)
+    assert lib.swp_server_poll(None, 1, ctypes.byref(done)) == S.EINVAL
+    assert b"server or done" in lib.swp_last_error()
+    assert lib.swp_server_stats(None, None) == S.EINVAL
+    assert lib.swp_server_destroy(None) == S.OK
