@@ -267,7 +267,8 @@ typedef struct {
                                  a request needing more than all of it fails
                                  with SWP_EBUDGET */
     int32_t max_active;       /* requests admitted at once (> 0) */
-    int32_t threads;          /* block size of the batched launches (0 = 256) */
+    int32_t threads;          /* block size of the batched launches (0 = the batch
+                                 defaults: 128 in FP64, 32 in FP32) */
     double round_target_ms;   /* GPU time aimed at per round (> 0) */
 } swp_server_config;
 
