@@ -30,6 +30,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -58,6 +59,7 @@ struct Request {
     double phase_cost = 0.0, credit = 0.0;   // estimated FP64 operations
     int state = 0;                       // 0 pending, 1 active, 2 done
     swp_status status = SWP_OK;
+    std::string error;                   // why it failed (handed to the waiter)
     swp_problem* prob = nullptr;
     size_t bytes = 0;                    // device bytes while active
     Clock::time_point t_submit, t_admit, t_done;
@@ -115,6 +117,8 @@ void swp_server::admit()
         if (cfg.hbm_budget_bytes && need > cfg.hbm_budget_bytes) {
             pending.pop_front();
             r->status = SWP_EBUDGET;
+            r->error = "the request needs " + std::to_string(need) + " device bytes, more than the server's budget of " +
+                       std::to_string(cfg.hbm_budget_bytes);
             r->state = 2;
             r->t_done = Clock::now();
             r->u0.clear();
@@ -127,6 +131,7 @@ void swp_server::admit()
         swp_status st = swp_create(&r->desc, r->u0.data(), 0, stream, &p);
         if (st != SWP_OK) {
             r->status = st;
+            r->error = swp_last_error();
             r->state = 2;
             r->t_done = Clock::now();
             cv_done.notify_all();
@@ -139,6 +144,7 @@ void swp_server::admit()
             swp_destroy(p);
             r->prob = nullptr;
             r->status = SWP_EINVAL;
+            r->error = "no valid swept node width for the request's n_points";
             r->state = 2;
             r->t_done = Clock::now();
             cv_done.notify_all();
@@ -208,10 +214,12 @@ swp_status swp_server::round()
         if (st == SWP_OK) st = swp_batch_synchronize(batch);
         round_launches = swp_batch_kernel_launches(batch) - l0;
     }
+    const std::string round_error = st != SWP_OK ? swp_last_error() : "";
     for (size_t i = 0; i < active.size(); ++i) {
         Request& r = *active[i];
         if (st != SWP_OK) {
             r.status = st;
+            r.error = round_error;
             r.steps_done = r.steps_total;
             continue;
         }
@@ -238,6 +246,7 @@ void swp_server::retire_finished()
         if (r->status == SWP_OK) {
             r->result.resize(state_bytes(r->desc));
             r->status = swp_read(r->prob, r->result.data(), r->result.size(), 0);
+            if (r->status != SWP_OK) r->error = swp_last_error();
         }
         swp_destroy(r->prob);
         r->prob = nullptr;
@@ -267,6 +276,7 @@ void swp_server::run()
                 // shutting down: fail what has not started
                 for (auto& r : pending) {
                     r->status = SWP_EINVAL;
+                    r->error = "the server shut down before admitting the request";
                     r->state = 2;
                     r->t_done = Clock::now();
                 }
@@ -360,7 +370,7 @@ swp_status swp_server_wait(swp_server* s, int64_t id, void* dst_host, size_t dst
         s->all.erase(id);
     }
     if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
-    if (r->status != SWP_OK) return swp::set_error(r->status, "the request failed (its status is returned)");
+    if (r->status != SWP_OK) return swp::set_error(r->status, r->error.c_str());
     if (dst_host) {
         if (dst_bytes < r->result.size()) return swp::set_error(SWP_EINVAL, "dst_bytes smaller than the state");
         std::memcpy(dst_host, r->result.data(), r->result.size());

@@ -80,3 +80,4 @@ def test_oversized_request_rejected_by_budget():
         with pytest.raises(S.SweptError) as e:
             srv.wait(rid)
         assert e.value.status == S.EBUDGET
+        assert "budget of 4096" in str(e.value)   # the scheduler's reason reaches the waiter
