@@ -40,3 +40,24 @@ def test_two_gloo_ranks_take_the_max_time():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert out == [(0, 1.25), (1, 1.25)]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Launched with N ranks, the reference arm (the CPU oracle) runs and
+    prints on rank 0 alone; the other ranks exit 0 without work."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for rank in (1, 0):
+        env = dict(os.environ, RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE="2",
+                   MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()))
+        r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2",
+                            "--steps", "1", "--warmup", "3"], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(r.stdout.strip())
+    assert outs[0] == ""
+    line = json.loads(outs[1].splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2
