@@ -315,7 +315,11 @@ swp_status swp_debug_withhold_flags(swp_problem* p, int withhold, int64_t wait_l
  *   desc             : problem description (as for swp_create)
  *   state            : DEVICE buffer of nv * N values ([nv][N], the dtype),
  *                      read as the initial state and overwritten with the
- *                      state after n_steps timesteps; owned by the caller
+ *                      state after n_steps timesteps; owned by the caller.
+ *                      The call has no size argument: the buffer must hold
+ *                      exactly that many values.  A pointer that is not
+ *                      device memory of the current device fails with
+ *                      SWP_EINVAL.
  *   points_per_block : node width as for swp_advance (0 = auto)
  *   threads          : threads per block (0 = auto)
  *   cuda_stream      : stream for the work (NULL = legacy default stream)
@@ -325,6 +329,9 @@ swp_status swp_debug_withhold_flags(swp_problem* p, int withhold, int64_t wait_l
  * library holds that array until the process exits.  The first call on a
  * device looks up the array's device address (set-up, once per device, with
  * that device current), so make that first call before any stream capture.
+ * That address belongs to the device's primary context: after
+ * cudaDeviceReset (or anything else that destroys that context) it is stale,
+ * so do not call this entry point on that device again in the process.
  * All calls share the one array, so calls whose GPU work overlaps (other
  * streams, other host threads) race and must be serialised by the caller.
  * No scratch value is read before the call writes it, so nothing needs

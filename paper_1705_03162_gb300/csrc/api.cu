@@ -1449,23 +1449,39 @@ constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// What the entry point needs to know about a device, looked up once per
+// device under the mutex: the scratch array's device address and the SM
+// count (the compute capability is checked at that time).
+struct NoAllocDevice {
+    void* scratch = nullptr;
+    int sms = 0;
+};
 std::mutex g_noalloc_mutex;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device `dev`, looked up
-// once per device.  In host code the array's name only stands in for the
-// symbol; the kernel must be given this address.
-swp_status noalloc_scratch(int dev, void** out)
+// Set-up for the current device `dev`, once per device.  In host code the
+// array's name only stands in for the symbol; the kernel must be given the
+// address that cudaGetSymbolAddress returns with that device current.
+swp_status noalloc_device(int dev, NoAllocDevice* out)
 {
     if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(SWP_EDEVICE, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.scratch) {
+        int major = 0, minor = 0, sms = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
+        if (major != 10 || minor != 3)
+            return fail(SWP_EDEVICE, "libswept is built for sm_103 (device is sm_%d%d)", major, minor);
         void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) return cuda_fail(e, "scratch symbol address");
-        g_noalloc_ptr[dev] = ptr;
+        d.sms = sms;
+        d.scratch = ptr;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = d;
     return SWP_OK;
 }
 
@@ -1484,14 +1500,21 @@ extern "C" swp_status swp_swept_noalloc(const swp_desc* desc, void* state, int64
                     "use swp_create / swp_advance for larger problems", sbytes, kNoAllocScratchBytes);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    cudaDeviceProp prop;
-    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, dev);
     if (e != cudaSuccess) return fail(SWP_EDEVICE, "no usable CUDA device: %s", cudaGetErrorString(e));
-    if (prop.major != 10 || prop.minor != 3)
-        return fail(SWP_EDEVICE, "libswept is built for sm_103 (device is sm_%d%d)", prop.major, prop.minor);
-    void* scratch = nullptr;
-    st = noalloc_scratch(dev, &scratch);
+    NoAllocDevice nd;
+    st = noalloc_device(dev, &nd);
     if (st != SWP_OK) return st;
+    void* scratch = nd.scratch;
+    // the state must be device memory of the current device (the kernels
+    // would otherwise read and write memory the caller did not mean)
+    cudaPointerAttributes pa;
+    e = cudaPointerGetAttributes(&pa, state);
+    if (e != cudaSuccess) {
+        cudaGetLastError();   // clear the (non-sticky) error this query recorded
+        return fail(SWP_EINVAL, "state is not a CUDA pointer: %s", cudaGetErrorString(e));
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != dev)
+        return fail(SWP_EINVAL, "state must be device memory of the current device %d", dev);
     if (n_steps == 0) return SWP_OK;
 
     // a problem record on the stack whose two level rows are the caller's
@@ -1508,7 +1531,7 @@ extern "C" swp_status swp_swept_noalloc(const swp_desc* desc, void* state, int64
     p.cur = 0;
     p.stream = (cudaStream_t)cuda_stream;
     p.device = dev;
-    p.sms = prop.multiProcessorCount;
+    p.sms = nd.sms;
     make_coefs<double>(desc, p.cd);
     make_coefs<float>(desc, p.cf);
     swp_advance_opts o;

@@ -295,11 +295,28 @@ def swept_noalloc(spec: ProblemSpec, state, steps: int, n: int = 0, threads: int
     """Advance the CUDA tensor ``state`` (shape (nv, N)) in place by ``steps``
     timesteps with the swept scheme through swp_swept_noalloc, which allocates
     no device memory (its scratch is a fixed 8 MiB array inside the library).
-    Asynchronous on ``stream``; calls that overlap on the GPU race."""
+    Asynchronous on ``stream``; calls that overlap on the GPU race.
+
+    swp_swept_noalloc takes no size argument, so the tensor is checked here
+    before any call: it must hold exactly nv * N values of ``dtype`` and live
+    on the current CUDA device."""
     lib = load_library()
     ptr, nbytes, dev = _buffer(state)
     if not dev:
         raise ValueError("state must be a CUDA tensor")
+    if dtype not in _DTYPE:
+        raise ValueError(f"unknown dtype {dtype!r}")
+    esize = 8 if dtype == "f64" else 4
+    want = spec.nv * spec.n_points * esize
+    if nbytes != want:
+        raise ValueError(f"state has {nbytes} bytes, expected {spec.nv} x {spec.n_points} x {esize} = {want}")
+    tdt = str(getattr(state, "dtype", ""))
+    if tdt != ("torch.float64" if dtype == "f64" else "torch.float32"):
+        raise ValueError(f"state dtype {tdt} does not match the problem dtype {dtype!r}")
+    index = getattr(getattr(state, "device", None), "index", None)
+    import torch
+    if index is None or index != torch.cuda.current_device():
+        raise ValueError(f"state is on device {index}, not the current CUDA device")
     desc = make_desc(spec, dtype)
     handle = getattr(stream, "cuda_stream", stream) if stream is not None else None
     _check(lib.swp_swept_noalloc(ctypes.byref(desc), ctypes.c_void_p(ptr), int(steps), int(n),

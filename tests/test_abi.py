@@ -177,3 +177,49 @@ def test_server_argument_errors_set_last_error(lib):
     assert b"server or done" in lib.swp_last_error()
     assert lib.swp_server_stats(None, None) == S.EINVAL
     assert lib.swp_server_destroy(None) == S.OK
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU: the binding's
+    checks of swept_noalloc run before any library or device call."""
+
+    def __init__(self, numel, esize, dtype, index=0):
+        self._numel, self._esize, self.dtype = numel, esize, dtype
+        self.is_cuda = True
+        self.device = type("Dev", (), {"index": index})()
+
+    def data_ptr(self):
+        return 0x10000
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._numel
+
+    def element_size(self):
+        return self._esize
+
+
+def test_noalloc_binding_checks_size_dtype_and_device(monkeypatch):
+    """swp_swept_noalloc takes no size argument, so the binding rejects a
+    state of the wrong size, dtype or device before calling it."""
+    torch = pytest.importorskip("torch")
+    spec = I.sod_spec(64)
+    calls = []
+    lib = S.load_library()
+    monkeypatch.setattr(S, "load_library", lambda: type("L", (), {
+        "swp_swept_noalloc": lambda *a: calls.append(a) or 0})())
+    with pytest.raises(ValueError, match="bytes"):
+        S.swept_noalloc(spec, _FakeCudaTensor(3 * 63, 8, "torch.float64"), 10)
+    with pytest.raises(ValueError, match="bytes"):   # float32 state passed as the default f64
+        S.swept_noalloc(spec, _FakeCudaTensor(3 * 64, 4, "torch.float32"), 10)
+    with pytest.raises(ValueError, match="dtype"):   # right size, wrong type
+        S.swept_noalloc(spec, _FakeCudaTensor(3 * 64 * 2, 4, "torch.float32"), 10)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    with pytest.raises(ValueError, match="device"):
+        S.swept_noalloc(spec, _FakeCudaTensor(3 * 64, 8, "torch.float64", index=1), 10)
+    assert calls == []
+    S.swept_noalloc(spec, _FakeCudaTensor(3 * 64, 8, "torch.float64"), 10)
+    assert len(calls) == 1
+    assert lib is not None
