@@ -21,68 +21,14 @@
  *    Dirichlet ghost cells (Appendix C).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off (no contraction of a*b+c into FMA:
- * every FMA is written out), no fast-math, -lm.
+ * every FMA is written out), no fast-math, -lm; the same source with
+ * -fopenmp is the all-core build, whose classic loops split each
+ * sub-timestep's points over threads (the bits do not change).
  */
-#include <math.h>
-#include <stdint.h>
-#include <stdlib.h>
-#include <string.h>
-
-#define ORC_OK 0
-#define ORC_EINVAL 1
-#define ORC_ENOMEM 2
-#define ORC_EUNSUPPORTED 5
-
-#define ORC_HEAT 0
-#define ORC_KS 1
-#define ORC_EULER 2
-
-#define ORC_BC_PERIODIC 0
-#define ORC_BC_REFLECTIVE 1
-#define ORC_BC_DIRICHLET 2
-
-#define ORC_F64 0
-#define ORC_F32 1
-
-/* Problem description (mirrors the fields a user gives when creating a
- * problem: equation, boundary condition, grid size, dx, dt, parameters). */
-typedef struct {
-    int32_t eq;
-    int32_t bc;
-    int64_t n_points;
-    double dx;
-    double dt;
-    double alpha;      /* heat: thermal diffusivity */
-    double gamma;      /* Euler: heat capacity ratio */
-    double left[3];    /* Euler Dirichlet end states, primitive (rho, u, p) */
-    double right[3];
-} orc_problem;
-
-/* Geometry of the swept plan (Sections 4.2-4.3) for nodes of n points and a
- * stencil of radius rad (sub sub-timesteps per timestep): H sub-timestep
- * levels per half-cycle, so an upright triangle of H - 1 levels above its base
- * advances H / sub timesteps; each node works in two rows of W = n + 2 rad
- * slots; `steps` timesteps take Q full half-cycles plus r remaining levels,
- * in `kernels` kernels (triangle, diamonds, closing triangle). */
-typedef struct {
-    int64_t H, W, Q, r, kernels, triangle_steps;
-} orc_geometry;
-
-static int swept_geometry(int rad, int sub, int64_t n, int64_t steps, orc_geometry* g)
-{
-    if (n <= 0 || n % (2 * rad) || steps < 0) return ORC_EINVAL;
-    g->H = n / (2 * rad);
-    /* H even keeps the level parity of every kernel's base level even, so the
-     * predictor / final alternation and the two rows line up in every node */
-    if (g->H & 1) return ORC_EINVAL;
-    g->W = n + 2 * rad;
-    int64_t T = steps * sub;
-    g->Q = T / g->H;
-    g->r = T % g->H;
-    g->kernels = T == 0 ? 0 : (g->r > 0 ? g->Q + 2 : g->Q + 1);
-    g->triangle_steps = g->H / sub;
-    return ORC_OK;
-}
+#include "oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* FP64 instantiation */
 #define REAL double
@@ -126,6 +72,19 @@ static int check_problem(const orc_problem* pb)
     return ORC_OK;
 }
 
+/* Threads of the classic loops in the OpenMP build (built with -fopenmp);
+ * the serial build ignores the request.  Returns the count in use. */
+int orc_set_threads(int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+    return omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
 /* Advance `state` (nv x N, SoA, in place) by `steps` timesteps with the
  * classic decomposition. */
 int orc_classic(const orc_problem* pb, int32_t dtype, void* state, int64_t steps)
@@ -164,6 +123,25 @@ int orc_swept_geometry(int32_t eq, int64_t n, int64_t steps, int64_t* out)
     out[3] = g.r;
     out[4] = g.kernels;
     out[5] = g.triangle_steps;
+    return ORC_OK;
+}
+
+/* One sub-timestep at one point (FP64), as the classic scheme evaluates it:
+ * the problem's coefficients (formed as for a whole run) and the point update
+ * of stage `stage` (0 predictor, 1 final; heat has only stage 0).
+ *   st   : the 2 rad + 1 stencil values, point-major (nv values per point)
+ *   base : nv values of the point at the start of the timestep (KS / Euler)
+ *   out  : nv values
+ * For the pins that compare one stage with the paper's formula in exact
+ * arithmetic. */
+int orc_stage_f64(const orc_problem* pb, int32_t stage, const double* st, const double* base, double* out)
+{
+    int e = check_problem(pb);
+    if (e) return e;
+    if (!st || !base || !out || stage < 0 || stage > 1) return ORC_EINVAL;
+    coefs_f64 c;
+    make_coefs_f64(pb, &c);
+    point_update_f64(&c, stage, st, base, out);
     return ORC_OK;
 }
 

@@ -3,8 +3,9 @@
 Each case plants one mistake, of the kind a restatement of the paper's
 schemes could plausibly contain (a dropped term, a wrong sign, a wrong or
 swapped index, a transposed operand), in a temporary copy of the oracle's
-source on the CPU. It then runs the pins (test_oracle_pins.py) against that
-copy, and at least one pin must fail. An unmutated copy must pass. The
+source on the CPU. It then runs the pins (test_oracle_pins.py, and
+test_oracle_literal.py, the exact-arithmetic check of one stage against the
+printed formulas) against that copy, and at least one pin must fail. An unmutated copy must pass. The
 schemes are those of arXiv:1705.03162 Appendices A-C and Sections 4-5; each
 case names the passage its mistake breaks. CPU only: nothing here touches a
 GPU or the CUDA library.
@@ -68,6 +69,12 @@ MUTATIONS = [
      "int64_t kr = odd ? k : (k + 1) % K;", "int64_t kr = k;"),
     ("swept: final-stage base from the source row", "Section 4.3 with Appendix B Eq. RKf",
      "base[v] = (stage == 0) ? src[v * W + q] : row0[v * W + q];", "base[v] = src[v * W + q];"),
+    # rounding-level mistakes: the equation is kept, an exact regrouping is
+    # replaced by a lossy one (only the exact-arithmetic pin sees these)
+    ("KS: combined weight beta rounded to single precision", "Appendix B Eq. KSDisc",
+     "c->beta[s] = (REAL)(a2 - 4.0 * a4);", "c->beta[s] = (REAL)(float)(a2 - 4.0 * a4);"),
+    ("Euler: update coefficient rounded to single precision", "Appendix C, the finite-volume update",
+     "c->kh[s] = (REAL)(-(0.5 * lamh));", "c->kh[s] = (REAL)(float)(-(0.5 * lamh));"),
 ]
 
 
@@ -77,7 +84,7 @@ def _run_pins(tmp_root: str, old: str, new: str):
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(tmp_root, "oracle"),
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
     os.makedirs(os.path.join(tmp_root, "tests"))
-    for f in ("test_oracle_pins.py", "riemann_exact.py", "conftest.py"):
+    for f in ("test_oracle_pins.py", "test_oracle_literal.py", "helpers.py", "riemann_exact.py", "conftest.py"):
         shutil.copy(os.path.join(ROOT, "tests", f), os.path.join(tmp_root, "tests", f))
     if old is not None:
         path = os.path.join(tmp_root, "oracle", "scheme.inc")
@@ -87,7 +94,8 @@ def _run_pins(tmp_root: str, old: str, new: str):
     # the copy's conftest puts tmp_root first on sys.path, so `oracle` is the
     # copy; the input generators come from the repository
     env = dict(os.environ, PYTHONPATH=ROOT)
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q",
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_oracle_literal.py",
+                        "-x", "-q",
                         "-p", "no:cacheprovider"], cwd=tmp_root, env=env, capture_output=True,
                        text=True, timeout=600)
     lines = (r.stdout + r.stderr).strip().splitlines()
