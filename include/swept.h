@@ -63,7 +63,8 @@ typedef enum { SWP_F64 = 0, SWP_F32 = 1 } swp_dtype;   /* Euler: SWP_F64 only */
 
 /* SWP_SCHEME_AUTO: the scheme (and width) swp_autotune measured faster for
  * the problem's (equation, dtype, n_points); swept at the tuned or default
- * width when none was measured. */
+ * width when none was measured; classic when N is too small for any swept
+ * node width. */
 typedef enum { SWP_CLASSIC = 0, SWP_SWEPT = 1, SWP_SCHEME_AUTO = 2 } swp_scheme;
 
 /* Problem description.
@@ -136,9 +137,15 @@ swp_status swp_create(const swp_desc* desc, const void* u0, int u0_on_device,
 swp_status swp_write(swp_problem* p, const void* src, size_t src_bytes, int src_on_device);
 
 /* Advance n_steps timesteps (any n_steps >= 0) with `scheme`.
- * Swept: points_per_block = n must divide N, be a multiple of 4 * radius
- * (radius 1 for heat, 2 for KS/Euler) and leave every node's working set in
- * shared memory; 0 picks a width.  The advance ends on a closing triangle, so
+ * Swept: points_per_block = n must be a multiple of 4 * radius (radius 1 for
+ * heat, 2 for KS/Euler) and leave every node's working set in shared memory.
+ * N need not be a multiple of n (the paper's nodes, Section 4.2, need it):
+ * the N = K n + d points form K = floor(N / n) nodes, node k starting at
+ * k n + floor(k d / K), so some are wider (by at most ceil(d / K) points);
+ * such a split needs K >= 2.
+ * 0 picks a width (the tuned one, else a default); when N is too small for
+ * any (fewer than two nodes of 4 * radius points) the advance runs the
+ * classic scheme, whose result is the same.  The advance ends on a closing triangle, so
  * the state is complete afterwards (Section 4.2: output only at closing
  * triangles); a final partial half-cycle is closed exactly.
  * Asynchronous on the problem's stream.  SWP_ETIMEOUT reports a persistent
@@ -201,8 +208,10 @@ typedef struct swp_batch swp_batch;
 swp_status swp_batch_create(void* cuda_stream, swp_batch** out);
 
 /* Advance problems[i] by n_steps[i] timesteps (swept), i < count.
- * points_per_block: per-problem node widths, or NULL / 0 entries for the
- * tuned width of swp_autotune_width (else the default rule).  threads: block
+ * points_per_block: per-problem node widths (any width swp_advance accepts),
+ * or NULL / 0 entries for the tuned width of swp_autotune_width (else the
+ * default rule; a problem too small for any node width runs as classic
+ * items, with the same result).  threads: block
  * size (0 = 128 for FP64 and 32 for FP32; Euler at most 256).  Problems must be distinct.  Asynchronous;
  * SWP_ETIMEOUT surfaces at swp_batch_synchronize (wait bound as for
  * swp_advance's persistent launch, SWP_WAIT_LIMIT_NS included). */
@@ -214,7 +223,8 @@ swp_status swp_batch_advance(swp_batch* b, swp_problem* const* problems, const i
  *                      (NULL = all SWP_SCHEME_AUTO)
  *   points_per_block : swept node width / classic chunk width m (4 <= m <= N)
  *                      per problem; NULL or 0 = the tuned width, else the
- *                      default (classic: min(N, 1024), Euler min(N, 256))
+ *                      default (classic: min(N, 1024), Euler min(N, 256);
+ *                      swept as for swp_batch_advance)
  *   launch           : SWP_LAUNCH_AUTO or _PERSISTENT (upload the task table
  *                      and launch), or SWP_LAUNCH_GRAPH: the launch is
  *                      captured as a CUDA graph with tables of its own on the
@@ -282,7 +292,9 @@ typedef struct {
 /* Start a server whose GPU work runs on cuda_stream of the current device. */
 swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, swp_server** out);
 /* Queue a solve of n_steps (>= 1) timesteps from u0_host (copied before the
- * call returns); request_id receives its id.  Thread-safe. */
+ * call returns); request_id receives its id.  Any N is served: swept at the
+ * tuned or default width (wider nodes take the remainder), classic when N is
+ * too small for any node width.  Thread-safe. */
 swp_status swp_server_submit(swp_server* s, const swp_desc* desc, const void* u0_host, int64_t n_steps,
                              int64_t* request_id);
 /* done = 1 once the request has finished (successfully or not). */

@@ -165,25 +165,43 @@ size_t max_smem(int device)
     return (size_t)v;
 }
 
-// A swept node width must divide N, be a multiple of 4 rad (so that H is
-// even) and fit the node's working set in shared memory.
+// Widest tile of nodes of n points over N: K = floor(N / n) nodes, the
+// remainder d = N - K n spread over them (node k starts at k n + floor(k d / K)).
+int64_t widest_node(int64_t N, int n)
+{
+    const int64_t K = N / n, d = N - K * n;
+    return K > 0 ? n + (d + K - 1) / K : 0;
+}
+
+// A swept node width must be a multiple of 4 rad (so that H is even), give at
+// least one node (two when it does not divide N: the wider nodes' tiles then
+// never meet themselves across the periodic wrap) and fit the widest node's
+// working set in shared memory.  It need not divide N: the remainder widens
+// some nodes.
 swp_status check_width(const swp_problem* p, int n)
 {
     const int step = 4 * p->rad;
     if (n < step || n % step) return fail(SWP_EINVAL, "points_per_block %d must be a positive multiple of %d", n, step);
-    if (p->N % n) return fail(SWP_EINVAL, "points_per_block %d must divide n_points %lld", n, (long long)p->N);
-    if (p->N / n > 0x7FFFFFFF) return fail(SWP_EINVAL, "points_per_block %d gives more than 2^31 - 1 nodes", n);
-    if (swept_smem_bytes(p->desc.eq, n, p->esize) > max_smem(p->device))
-        return fail(SWP_EINVAL, "points_per_block %d needs %zu bytes of shared memory (max %zu)", n,
-                    swept_smem_bytes(p->desc.eq, n, p->esize), max_smem(p->device));
+    const int64_t K = p->N / n, d = p->N % n;
+    if (K < 1) return fail(SWP_EINVAL, "points_per_block %d exceeds n_points %lld", n, (long long)p->N);
+    if (d != 0 && K < 2)
+        return fail(SWP_EINVAL, "points_per_block %d leaves one node for n_points %lld, which it does not divide", n,
+                    (long long)p->N);
+    if (K > 0x7FFFFFFF) return fail(SWP_EINVAL, "points_per_block %d gives more than 2^31 - 1 nodes", n);
+    const int64_t wide = widest_node(p->N, n);
+    if (wide > (1 << 20) || swept_smem_bytes(p->desc.eq, (int)wide, p->esize) > max_smem(p->device))
+        return fail(SWP_EINVAL, "points_per_block %d (widest node %lld) needs more shared memory than a block has", n,
+                    (long long)wide);
     return SWP_OK;
 }
 
 // Default node width, from the widths measured fastest on GB300 for single
 // problems: about N / 1024 points for heat and KS (N / 512 in the persistent
 // dataflow launch; at least 64 and 128, at most 1024) and N / 256 for Euler
-// (64 to 512); the nearest width that divides N, is a multiple of 4 rad and
-// fits shared memory.
+// (64 to 512).  The nearest width down to half the target that divides N and
+// is a multiple of 4 rad; else the target itself (rounded down to a multiple
+// of 4 rad), whose remainder widens some nodes; 0 when N is too small for
+// any (fewer than two nodes of 4 rad points).
 int default_width(const swp_problem* p, bool dataflow = false)
 {
     const int step = 4 * p->rad;
@@ -194,10 +212,10 @@ int default_width(const swp_problem* p, bool dataflow = false)
     if (target < lo) target = lo;
     if (target > cap) target = cap;
     if (target > p->N / 2) target = p->N / 2;
-    for (int64_t n = target; n >= step; --n)
+    for (int64_t n = target; n >= step && 2 * n >= target; --n)
         if (n % step == 0 && p->N % n == 0 && check_width(p, (int)n) == SWP_OK) return (int)n;
-    for (int64_t n = target + 1; n <= cap && n <= p->N; ++n)
-        if (n % step == 0 && p->N % n == 0 && check_width(p, (int)n) == SWP_OK) return (int)n;
+    for (int64_t n = target / step * step; n >= step; n -= step)
+        if (check_width(p, (int)n) == SWP_OK) return (int)n;
     return 0;
 }
 
@@ -235,7 +253,7 @@ int default_chunk(const swp_problem* p)
 }
 
 // SWP_SCHEME_AUTO: the scheme swp_autotune measured faster (with its width),
-// else swept at width_for.
+// else swept at width_for, else (N too small for any node width) classic.
 void choice_for(const swp_problem* p, int* scheme, int* n)
 {
     Tuned t;
@@ -246,6 +264,10 @@ void choice_for(const swp_problem* p, int* scheme, int* n)
     }
     *scheme = SWP_SWEPT;
     *n = width_for(p);
+    if (*n == 0) {
+        *scheme = SWP_CLASSIC;
+        *n = default_chunk(p);
+    }
 }
 
 template <typename R>
@@ -285,6 +307,7 @@ swp_status run_classic(swp_problem* p, int64_t steps, int threads)
 
 struct SweptPlan {
     int n, H, K;
+    int d;     // N - K n, spread over the nodes (0 when n divides N)
     int64_t T, Q, r, n_phases;
     int top;   // relative level of the last phase's top row
 };
@@ -295,12 +318,29 @@ SweptPlan plan_swept(const swp_problem* p, int64_t steps, int n)
     s.n = n;
     s.H = n / (2 * p->rad);
     s.K = (int)(p->N / n);
+    s.d = (int)(p->N - (int64_t)s.K * n);
     s.T = steps * p->sub;
     s.Q = s.T / s.H;
     s.r = s.T % s.H;
     s.n_phases = s.r > 0 ? s.Q + 2 : s.Q + 1;
     s.top = s.r > 0 ? (int)s.r : s.H;
     return s;
+}
+
+// Geometry of phase ph of a plan.  Even phases of a plan with wider nodes
+// (d > 0) also compute level 2H, the wider nodes' middle points.
+PhaseGeom phase_geom(const swp_problem* p, const SweptPlan& s, int64_t ph)
+{
+    PhaseGeom g;
+    g.N = p->N;
+    g.n = s.n;
+    g.H = s.H;
+    g.K = s.K;
+    g.d = s.d;
+    g.odd = (int)(ph & 1);
+    g.j_lo = ph == 0 ? s.H + 1 : 1;
+    g.j_hi = ph < s.Q ? 2 * s.H - 1 + (!g.odd && s.d ? 1 : 0) : (ph == s.Q ? s.H + (int)s.r : (int)s.r);
+    return g;
 }
 
 template <typename R>
@@ -310,14 +350,7 @@ swp_status run_swept_register(swp_problem* p, const SweptPlan& s, int threads)
     R* B = (R*)p->rows[1 - p->cur];
     const Coefs<R>& c = coefs_of<R>(p);
     for (int64_t ph = 0; ph < s.n_phases; ++ph) {
-        PhaseGeom g;
-        g.N = p->N;
-        g.n = s.n;
-        g.H = s.H;
-        g.K = s.K;
-        g.j_lo = ph == 0 ? s.H + 1 : 1;
-        g.j_hi = ph < s.Q ? 2 * s.H - 1 : (ph == s.Q ? s.H + (int)s.r : (int)s.r);
-        g.odd = (int)(ph & 1);
+        const PhaseGeom g = phase_geom(p, s, ph);
         cudaError_t e = launch_swept_register<R>(p->desc.eq, A, B, g, c, threads, p->stream);
         p->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "register swept launch");
@@ -334,14 +367,7 @@ swp_status run_swept_phases(swp_problem* p, const SweptPlan& s, int threads, int
     const Coefs<R>& c = coefs_of<R>(p);
     if (p_hi < 0) p_hi = s.n_phases;
     for (int64_t ph = p_lo; ph < p_hi; ++ph) {
-        PhaseGeom g;
-        g.N = p->N;
-        g.n = s.n;
-        g.H = s.H;
-        g.K = s.K;
-        g.j_lo = ph == 0 ? s.H + 1 : 1;
-        g.j_hi = ph < s.Q ? 2 * s.H - 1 : (ph == s.Q ? s.H + (int)s.r : (int)s.r);
-        g.odd = (int)(ph & 1);
+        const PhaseGeom g = phase_geom(p, s, ph);
         cudaError_t e = launch_swept_phase<R>(p->desc.eq, p->desc.bc, A, B, g, c, threads, p->stream);
         p->launches++;
         if (e != cudaSuccess) return cuda_fail(e, "swept phase launch");
@@ -456,6 +482,13 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         int n = 0;
         choice_for(p, &o.scheme, &n);
         if (o.scheme == SWP_SWEPT && o.points_per_block == 0) o.points_per_block = n;
+    }
+    if (o.scheme == SWP_SWEPT && o.points_per_block == 0 && o.launch != SWP_LAUNCH_REGISTER &&
+        default_width(p) == 0) {
+        // N is too small for two nodes of 4 rad points: the classic scheme,
+        // whose result is the same
+        o.scheme = SWP_CLASSIC;
+        if (o.launch != SWP_LAUNCH_GRAPH) o.launch = SWP_LAUNCH_AUTO;
     }
     if (o.scheme == SWP_CLASSIC) {
         if (o.launch == SWP_LAUNCH_GRAPH) {
@@ -875,6 +908,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         in.n = it.s.n;
         in.H = it.s.H;
         in.K = it.s.K;
+        in.d = it.kind == BATCH_SWEPT ? it.s.d : 0;
         in.bc = it.p->desc.bc;
         in.Q = it.s.Q;
         in.r = it.s.r;
@@ -886,7 +920,8 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
         in.c = coefs_of<R>(it.p);
         flags += it.s.K;
         items_total += (it.p_hi - it.p_lo) * it.s.K;
-        smem = std::max(smem, it.kind == BATCH_SWEPT ? swept_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize)
+        smem = std::max(smem, it.kind == BATCH_SWEPT
+                                  ? swept_smem_bytes(it.p->desc.eq, (int)widest_node(it.p->N, it.s.n), it.p->esize)
                                                      : batch_classic_smem_bytes(it.p->desc.eq, it.s.n, it.p->esize));
     }
     // (instance, phase) tasks in order of estimated start: phase p of instance
@@ -1107,9 +1142,11 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
         }
         BatchItem it;
         it.p = p;
+        if (scheme == SWP_SWEPT && n == 0) {
+            n = width_for(p);
+            if (n == 0) scheme = SWP_CLASSIC;   // N too small for any node width: classic items
+        }
         if (scheme == SWP_SWEPT) {
-            if (n == 0) n = width_for(p);
-            if (n == 0) return fail(SWP_EINVAL, "no valid node width for problem %d", i);
             swp_status st = check_width(p, n);
             if (st != SWP_OK) return st;
             it.kind = BATCH_SWEPT;
@@ -1207,9 +1244,11 @@ namespace swp {
 
 int swept_width(const swp_problem* p) { return width_for(p); }
 
-int64_t swept_phase_count(const swp_problem* p, int64_t steps, int n)
+int classic_chunk(const swp_problem* p) { return default_chunk(p); }
+
+int64_t phase_count(const swp_problem* p, int64_t steps, int kind, int n)
 {
-    return plan_swept(p, steps, n).n_phases;
+    return kind == BATCH_CLASSIC ? plan_classic(p, steps, n).n_phases : plan_swept(p, steps, n).n_phases;
 }
 
 swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads)
@@ -1221,19 +1260,23 @@ swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int coun
         swp_problem* p = r.p;
         if (!p || p->device != b->device || p->stream != b->stream)
             return fail(SWP_EINVAL, "range %d: problem NULL or on another device / stream", i);
-        swp_status st = check_width(p, r.n);
+        const bool classic = r.kind == BATCH_CLASSIC;
+        swp_status st = classic ? check_chunk(p, r.n) : check_width(p, r.n);
         if (st != SWP_OK) return st;
         BatchItem it;
         it.p = p;
-        it.kind = BATCH_SWEPT;
-        it.s = plan_swept(p, r.steps, r.n);
+        it.kind = classic ? BATCH_CLASSIC : BATCH_SWEPT;
+        it.s = classic ? plan_classic(p, r.steps, r.n) : plan_swept(p, r.steps, r.n);
         if (r.p_lo < 0 || r.p_hi > it.s.n_phases || r.p_lo > r.p_hi)
             return fail(SWP_EINVAL, "range %d: phases [%lld, %lld) outside the plan", i, (long long)r.p_lo,
                         (long long)r.p_hi);
         if (r.p_lo == r.p_hi) continue;
         it.p_lo = r.p_lo;
         it.p_hi = r.p_hi;
-        it.flip = r.p_hi == it.s.n_phases && (it.s.top & 1);
+        // the state moves to the other row once the whole plan has run: swept
+        // when its last level is odd, classic heat after an odd step count
+        it.flip = r.p_hi == it.s.n_phases &&
+                  (classic ? (p->desc.eq == SWP_HEAT && (it.s.T & 1)) : (it.s.top & 1) != 0);
         groups[p->desc.eq == SWP_EULER ? 1 : 0][p->desc.dtype].push_back(it);
     }
     return launch_groups(b, groups, threads, false);

@@ -27,12 +27,13 @@ struct PhaseGeom {
     int64_t N;      // points
     int n;          // node width (points per node)
     int H;          // sub-timestep levels per half-cycle, n / (2 radius)
-    int K;          // nodes, N / n
+    int K;          // nodes, floor(N / n)
+    int d;          // N - K n: node k starts at k n + floor(k d / K)
     int j_lo, j_hi; // levels computed, relative to the phase's base level
-    int odd;        // 1: nodes centred on node boundaries; 0: on node centres
+    int odd;        // 1: tiles centred on node boundaries; 0: a tile per node
 };
 
-// Shared memory a swept phase kernel needs for node width n.
+// Shared memory a swept phase kernel needs for tiles of at most n points.
 size_t swept_smem_bytes(int eq, int n, int elem_bytes);
 
 // One phase over all K nodes: every block loads its node's window of the two
@@ -65,6 +66,7 @@ template <typename R> struct BatchInst {
     R* B;                 // swept: odd-level row; classic: the other row
     int64_t N;
     int n, H, K, bc;      // classic: n = widest chunk, H unused, K chunks
+    int d;                // swept: N - K n (wider nodes, see PhaseGeom); classic: 0
     int64_t Q, r, n_phases;  // classic: n_phases = sub-timesteps, Q = r = 0
     int64_t phase_lo;     // first phase of this launch (the earlier ones ran in earlier launches)
     int flag_off;         // first flag of this instance
@@ -104,20 +106,24 @@ int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads
 // shared memory (Euler, or n not split that way).
 int swept_reg_slots(int eq, int n, int threads, int elem_bytes);
 
-// Open swept advances in pieces (the serving loop): a range runs phases
-// [p_lo, p_hi) of the swept plan for `steps` timesteps at node width n.
-// Between pieces the problem's two rows hold the open state (triangle edges);
-// it is complete, and bit-identical to one swp_advance of `steps` at width n,
-// after the plan's last phase has run.  All pieces of one problem use the same
-// (steps, n) and run in order on the batch's stream.
+// Open advances in pieces (the serving loop): a range runs phases
+// [p_lo, p_hi) of the plan for `steps` timesteps: swept at node width n, or
+// (kind BATCH_CLASSIC, for N too small for any node width) classic in chunks
+// of n points, a phase per sub-timestep.  Between pieces the problem's two
+// rows hold the open state (triangle edges, or the predictor row); it is
+// complete, and bit-identical to one swp_advance of `steps` with that scheme,
+// after the plan's last phase has run.  All pieces of one problem use the
+// same (kind, steps, n) and run in order on the batch's stream.
 struct PhaseRange {
     swp_problem* p;
     int n;
     int64_t steps;
     int64_t p_lo, p_hi;
+    int kind;   // BatchKind
 };
-int swept_width(const swp_problem* p);   // the tuned or default node width
-int64_t swept_phase_count(const swp_problem* p, int64_t steps, int n);
+int swept_width(const swp_problem* p);    // the tuned or default node width (0: none)
+int classic_chunk(const swp_problem* p);  // the default classic chunk width
+int64_t phase_count(const swp_problem* p, int64_t steps, int kind, int n);
 swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads);
 // The same for one problem, as per-phase launches on its own stream.
 swp_status advance_phases(swp_problem* p, int n, int64_t steps, int64_t p_lo, int64_t p_hi);

@@ -54,7 +54,8 @@ struct Request {
     std::vector<unsigned char> u0;       // host copy of the initial state
     std::vector<unsigned char> result;   // host copy of the final state
     int64_t steps_total = 0, steps_done = 0;
-    int n = 0;                           // node width of the request's swept plan
+    int n = 0;                           // node width of the request's swept plan (classic: chunk width)
+    int kind = swp::BATCH_SWEPT;         // BATCH_CLASSIC when N is too small for any node width
     int64_t n_phases = 0, phase_next = 0;
     double phase_cost = 0.0, credit = 0.0;   // estimated FP64 operations
     int state = 0;                       // 0 pending, 1 active, 2 done
@@ -139,12 +140,17 @@ void swp_server::admit()
         }
         r->prob = p;
         r->n = swp::swept_width(p);
-        r->n_phases = r->n > 0 ? swp::swept_phase_count(p, r->steps_total, r->n) : 0;
+        r->kind = swp::BATCH_SWEPT;
+        if (r->n == 0) {   // too few points for two swept nodes: the classic plan
+            r->kind = swp::BATCH_CLASSIC;
+            r->n = swp::classic_chunk(p);
+        }
+        r->n_phases = swp::phase_count(p, r->steps_total, r->kind, r->n);
         if (r->n_phases <= 0) {
             swp_destroy(p);
             r->prob = nullptr;
             r->status = SWP_EINVAL;
-            r->error = "no valid swept node width for the request's n_points";
+            r->error = "the request's plan has no phases";
             r->state = 2;
             r->t_done = Clock::now();
             cv_done.notify_all();
@@ -191,7 +197,7 @@ swp_status swp_server::round()
         if (take[i] <= 0) continue;
         Request& r = *active[i];
         r.credit -= (double)take[i] * r.phase_cost;
-        ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i]});
+        ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i], r.kind});
     }
     const int64_t l0 = swp_batch_kernel_launches(batch);
     int64_t round_launches = 0;
@@ -201,7 +207,8 @@ swp_status swp_server::round()
     if (ranges.size() == 1)
         for (auto& rq : active)
             if (rq->prob == ranges[0].p)
-                solo_phases = rq->desc.n_points < ((int64_t)1 << 17) || rq->desc.dtype == SWP_F32;
+                solo_phases = rq->kind == swp::BATCH_SWEPT &&
+                              (rq->desc.n_points < ((int64_t)1 << 17) || rq->desc.dtype == SWP_F32);
     if (solo_phases) {
         // as swp_advance would run it alone (SWP_LAUNCH_AUTO)
         const swp::PhaseRange& r = ranges[0];

@@ -27,6 +27,17 @@
 // of phase p-1.  At the end A (or B, when the last level is odd) holds the
 // full state.
 //
+// Any N.  The paper's nodes all have n points, so N must be a multiple of n.
+// Here N = K n + d with 0 <= d < n: node k covers [b_k, b_{k+1}) with
+// b_k = k n + floor(k d / K), so d nodes are one point (or a few points)
+// wider.  Odd-phase tiles keep width n, centred on the node boundaries b_k;
+// an even-phase tile spans its whole node and computes level j on
+// [b_k + rad |j - H|, b_{k+1} - rad |j - H|): a triangle for a node of n
+// points, a trapezoid for a wider one, which also computes level 2H on its
+// middle points (the gap between the two odd tiles beside it).  Locally the
+// geometry is the equal-width one, so the two rows still hold, at every
+// position, the latest level of each parity that the next tile reads.
+//
 // Boundaries.  Periodic problems wrap the window modulo N.  For reflective or
 // Dirichlet ends, the node straddling x = 0 (first node of odd phases, the
 // paper's split node) and the first/last nodes of even phases (whose widest
@@ -45,6 +56,28 @@ template <int EQ> struct Shape {
 };
 
 __host__ __device__ __forceinline__ int window_width(int n, int rad) { return n + 2 * rad; }
+
+// First point of node k of the K nodes of n points (plus the remainder d
+// spread over them) that partition [0, N).
+__host__ __device__ __forceinline__ int64_t node_start(int64_t k, int n, int K, int d)
+{
+    return k * n + (k * d) / K;
+}
+
+// Window of the tile of node k in a phase: global point of slot 0 and the
+// tile's width nk (slots [rad, rad + nk) are its points).  Odd phases: n
+// points centred on the node boundary b_k; even phases: the whole node.
+__device__ __forceinline__ void tile_window(int k, int odd, int n, int K, int d, int rad, int64_t& g0, int& nk)
+{
+    const int64_t b = node_start(k, n, K, d);
+    if (odd) {
+        g0 = b - n / 2 - rad;
+        nk = n;
+    } else {
+        g0 = b - rad;
+        nk = (int)(node_start(k + 1, n, K, d) - b);
+    }
+}
 
 __device__ __forceinline__ int64_t wrap(int64_t g, int64_t N)
 {
@@ -140,9 +173,9 @@ __device__ __forceinline__ void row_copy(R* row, int64_t N, int64_t g, int count
     }
 }
 
-// Load the node window of rows A / B (global, [NV][N]) into shared memory.
-// Row 0 (A) occupies slots [rad, rad + n); row 1 (B) all W slots.  Coalesced
-// 16-byte vector loads (row_copy).
+// Load the window of a tile of n points from rows A / B (global, [NV][N])
+// into shared memory.  Row 0 (A) occupies slots [rad, rad + n); row 1 (B)
+// all W = n + 2 rad slots.  Coalesced 16-byte vector loads (row_copy).
 template <typename R, int EQ, bool CG>
 __device__ __forceinline__ void window_load(const R* A, const R* B, R* row0, R* row1, int n,
                                             int64_t g0, int64_t N, bool need_b)
@@ -156,8 +189,9 @@ __device__ __forceinline__ void window_load(const R* A, const R* B, R* row0, R* 
     }
 }
 
-// Write back what the node may have changed: row 0 slots [rad, rad + n) and
-// row 1 slots [2 rad, n) (the odd levels of its upright triangle).
+// Write back what a tile of n points may have changed: row 0 slots
+// [rad, rad + n) and row 1 slots [2 rad, n) (the odd levels of its upright
+// triangle).
 template <typename R, int EQ, bool CG>
 __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R* row1, int n,
                                              int64_t g0, int64_t N)
@@ -171,22 +205,24 @@ __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R*
     }
 }
 
-// Advance levels j_lo..j_hi of one node in shared memory.
-//   row0 / row1 : [NV][W] even / odd level rows
+// Advance levels j_lo..j_hi of one tile of nk points in shared memory.
+//   row0 / row1 : [NV][W] even / odd level rows, W = nk + 2 rad
 //   P, G        : Euler scratch, W pressures, [3][W + 1] + 3 interface values, 8 ghost values
 //   wall        : the node may evaluate points next to a non-periodic end
 template <typename R, int EQ>
-__device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int n, int H, int j_lo,
+__device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk, int H, int j_lo,
                                             int j_hi, int64_t g0, int64_t N, bool wall, int bc,
                                             const Coefs<R>& c)
 {
     constexpr int RAD = Shape<EQ>::RAD;
-    const int W = window_width(n, RAD);
-    const int cs = n / 2 + RAD;
+    const int W = window_width(nk, RAD);
     const int T = blockDim.x;
     for (int j = j_lo; j <= j_hi; ++j) {
-        const int w = RAD * (j <= H ? j : 2 * H - j);
-        const int lo = cs - w, cnt = 2 * w;
+        // level j on slots [rad (1 + |j - H|), rad + nk - rad |j - H|): for a
+        // tile of n = 2 rad H points, the 2 rad min(j, 2H - j) points around
+        // its centre
+        const int a = RAD * (j <= H ? H - j : j - H);
+        const int lo = RAD + a, cnt = nk - 2 * a;
         R* dst = (j & 1) ? row1 : row0;
         const R* src = (j & 1) ? row0 : row1;
         const int stage = (EQ == HEAT) ? 0 : ((j & 1) ? 0 : 1);
@@ -426,20 +462,21 @@ __device__ __forceinline__ bool node_near_wall(int bc, int k, int K)
     return bc != PERIODIC && (k == 0 || k == K - 1);
 }
 
-// Levels j_lo..j_hi of one node.  PR > 0: register-blocked with PR slots
-// per thread (heat and KS nodes away from non-periodic ends; blockDim.x * PR
-// == n, the host picks it); otherwise in shared memory.
+// Levels j_lo..j_hi of one tile of nk points (nodes of n).  PR > 0:
+// register-blocked with PR slots per thread (heat and KS tiles of n points
+// away from non-periodic ends; blockDim.x * PR == n, the host picks it);
+// otherwise in shared memory.
 template <typename R, int EQ, int PR>
-__device__ __forceinline__ void run_levels(R* row0, R* row1, R* P, R* G, int n, int H, int j_lo, int j_hi,
-                                           int64_t g0, int64_t N, bool wall, int bc, const Coefs<R>& c)
+__device__ __forceinline__ void run_levels(R* row0, R* row1, R* P, R* G, int n, int nk, int H, int j_lo,
+                                           int j_hi, int64_t g0, int64_t N, bool wall, int bc, const Coefs<R>& c)
 {
     if constexpr (PR > 0 && EQ != EULER) {
-        if (!wall) {
+        if (!wall && nk == n) {
             tile_levels_reg<R, EQ, PR>(row0, row1, P, n, H, j_lo, j_hi, c);
             return;
         }
     }
-    tile_levels<R, EQ>(row0, row1, P, G, n, H, j_lo, j_hi, g0, N, wall, bc, c);
+    tile_levels<R, EQ>(row0, row1, P, G, nk, H, j_lo, j_hi, g0, N, wall, bc, c);
 }
 
 template <typename R, int EQ, int PR>
@@ -448,17 +485,18 @@ __global__ void __launch_bounds__(EQ == EULER ? 256 : 1024) swept_phase_kernel(R
 {
     constexpr int RAD = Shape<EQ>::RAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *row0, *row1, *P, *G;
-    smem_rows<R, EQ>(smem_raw, g.n, row0, row1, P, G);
     const int k = blockIdx.x;
-    const int64_t xc = g.odd ? (int64_t)k * g.n : (int64_t)k * g.n + g.n / 2;
-    const int64_t g0 = xc - g.n / 2 - RAD;
+    int64_t g0;
+    int nk;
+    tile_window(k, g.odd, g.n, g.K, g.d, RAD, g0, nk);
+    R *row0, *row1, *P, *G;
+    smem_rows<R, EQ>(smem_raw, nk, row0, row1, P, G);
     const bool need_b = g.j_lo <= g.H;   // every phase but the first reads odd-level edges
-    window_load<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N, need_b);
+    window_load<R, EQ, false>(A, B, row0, row1, nk, g0, g.N, need_b);
     __syncthreads();
-    run_levels<R, EQ, PR>(row0, row1, P, G, g.n, g.H, g.j_lo, g.j_hi, g0, g.N,
-                       node_near_wall(bc, k, g.K), bc, c);
-    window_store<R, EQ, false>(A, B, row0, row1, g.n, g0, g.N);
+    run_levels<R, EQ, PR>(row0, row1, P, G, g.n, nk, g.H, g.j_lo, g.j_hi, g0, g.N,
+                          node_near_wall(bc, k, g.K), bc, c);
+    window_store<R, EQ, false>(A, B, row0, row1, nk, g0, g.N);
 }
 
 // ---------------------------------------------------------------------------
@@ -586,12 +624,15 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     const int H = in.H, n = in.n;
     const int odd = (int)(p & 1);
     const int j_lo = p == 0 ? H + 1 : 1;
-    const int j_hi = p < in.Q ? 2 * H - 1 : (p == in.Q ? H + (int)in.r : (int)in.r);
+    // even phases of a partition with wider nodes also compute level 2H (the
+    // wider nodes' middle points)
+    const int j_hi = p < in.Q ? 2 * H - 1 + (!odd && in.d ? 1 : 0) : (p == in.Q ? H + (int)in.r : (int)in.r);
+    int64_t g0;
+    int nk;
+    tile_window(k, odd, n, in.K, in.d, RAD, g0, nk);
     R *row0, *row1, *P, *G;
-    smem_rows<R, EQ>(smem_raw, n, row0, row1, P, G);
-    const int64_t xc = odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
-    const int64_t g0 = xc - n / 2 - RAD;
-    window_load<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N, j_lo <= H);
+    smem_rows<R, EQ>(smem_raw, nk, row0, row1, P, G);
+    window_load<R, EQ, true>(in.A, in.B, row0, row1, nk, g0, in.N, j_lo <= H);
     // heat / KS: the point-update coefficients in registers for all levels,
     // rather than re-read from the instance table after every level barrier
     Coefs<R> cr{};
@@ -609,7 +650,7 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     __syncthreads();
     bool done = false;
     if constexpr (REG && EQ != EULER) {
-        done = !node_near_wall(in.bc, k, in.K);
+        done = !node_near_wall(in.bc, k, in.K) && nk == n;
         if (done) switch (n / (int)blockDim.x) {
         case 2: tile_levels_reg<R, EQ, 2>(row0, row1, P, n, H, j_lo, j_hi, c); break;
         case 4: tile_levels_reg<R, EQ, 4>(row0, row1, P, n, H, j_lo, j_hi, c); break;
@@ -625,9 +666,9 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
         }
     }
     if (!done)
-        run_levels<R, EQ, 0>(row0, row1, P, G, n, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
+        run_levels<R, EQ, 0>(row0, row1, P, G, n, nk, H, j_lo, j_hi, g0, in.N, node_near_wall(in.bc, k, in.K),
                              in.bc, c);
-    window_store<R, EQ, true>(in.A, in.B, row0, row1, n, g0, in.N);
+    window_store<R, EQ, true>(in.A, in.B, row0, row1, nk, g0, in.N);
 }
 
 // Value of variable v at global point g (within rad of [0, N)) of a [NV][N]
@@ -810,7 +851,7 @@ template <typename R, int EQ, int PR>
 cudaError_t phase_launch_pr(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
                             cudaStream_t s)
 {
-    const size_t smem = sizeof(R) * smem_elems<EQ>(g.n);
+    const size_t smem = sizeof(R) * smem_elems<EQ>(g.n + (g.d + g.K - 1) / g.K);   // the widest node
     cudaError_t e = set_smem<R, EQ>((const void*)swept_phase_kernel<R, EQ, PR>, smem);
     if (e != cudaSuccess) return e;
     swept_phase_kernel<R, EQ, PR><<<g.K, threads, smem, s>>>(A, B, g, bc, c);
