@@ -39,26 +39,57 @@ METRIC = "G point-updates/s swept vs classic @2^20 pts (FP64); p50/p99 served so
 WORKLOAD = "KS N=2^20 {} 10^4 steps (dx=0.5, dt=0.005, u0=cos(x/16)(1+sin(x/16)))"
 UNIT = "G point-updates/s"
 
-# Floating-point operations of one KS point-update (two RK2 stages of seven
-# FP64 operations: four FMAs, three adds = 11 flops each).
-KS_FLOPS_PER_UPDATE = 22
-KS_FP64_OPS_PER_UPDATE = 14
-# FP64 pipe of GB300: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal
-# 1.25 TFLOP/s dense FP64 at the maximum SM clock).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Roofline denominators.  FP64 / FP32 pipes: measured on GB300 by a
+# microbenchmark of independent FMA chains (626 G DFMA/s = 1.253 TFLOP/s;
+# 78.3 TFLOP/s FFMA); the nominal 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz is
+# 1.259 TFLOP/s.  HBM: the measured copy bandwidth, read at run time.
+FP64_PEAK_TFLOPS = 1.253
+FP32_PEAK_TFLOPS = 78.3
+HBM_FALLBACK_GBS = 6800.0
+
+# Floating-point operations per point-update, counted by the CPU oracle's
+# counting build and stored as data (oracle/opcounts.json, written by
+# oracle/write_opcounts.py); read here as a table, never executed.
+OPCOUNTS_PATH = os.path.join(ROOT, "oracle", "opcounts.json")
+
+
+def _opcounts() -> dict:
+    with open(OPCOUNTS_PATH) as f:
+        return json.load(f)["counts"]
+
+
+def op_count(eq: str, what: str = "flops") -> float:
+    """Algorithmic flops (FMA = 2) or operations (FMA = 1) of one
+    point-update; Euler on the Sod workload shape of the benchmark."""
+    key = {"heat": "heat", "ks": "ks", "euler": "euler_sod_steps_over_n_1_256"}[eq]
+    return float(_opcounts()[key]["algorithmic"][what])
+
+
+def hbm_peak() -> tuple:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured)"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s"
+
+
+def alu_roofline(updates: float, seconds: float, eq: str, dtype: str) -> dict:
+    """Algorithmic flops per second against the pipe of the working
+    precision (every path here is bound by its FP pipe or by issue)."""
+    peak = FP32_PEAK_TFLOPS if dtype == "f32" else FP64_PEAK_TFLOPS
+    achieved = updates * op_count(eq) / seconds / 1e12
+    ops = updates * op_count(eq, "ops") / seconds / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "flops_per_update": op_count(eq), "pipe_ops_frac": ops / (peak / 2),
+            "peak_note": f"measured {'FP32' if dtype == 'f32' else 'FP64'} pipe"}
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
 # a hash of the kernel sources it was taken on (code only: comments and blank
 # lines do not count); reported as null once the code changes.
 NCU_TRAFFIC = {
-    # profiles/swept_phase_kernel_ks_n1024.md: dram__bytes_read.sum + dram__bytes_write.sum of a
-    # full-diamond launch (16.78 MB + 0), cold caches
-    "swept_phase_kernel<double,KS> n=1024 threads=256": {"src": "5e80a285e7a01b44", "bytes_per_launch": 16783872},
-    # profiles/swept_batch_kernel_ks_n1024.md: the whole 10^4-step solve in one dataflow launch,
-    # 1-pass capture of the bench's timed launch: 8.98 MB read + 2.67 MB written (ncu rounds to 10 kB)
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "62b75750d8ebfd2b", "bytes_per_launch": 11650000},
+    # dram__bytes_read.sum + dram__bytes_write.sum of the whole 10^4-step solve in
+    # one dataflow launch: a one-pass capture of the benchmark's own timed launch
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "380626afd303d2d7", "bytes_per_launch": 11968256},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
@@ -189,25 +220,41 @@ def _host_cpu() -> dict:
     return {"nproc": os.cpu_count(), "model": model, "arch": platform.machine()}
 
 
-def cpu_oracle_rate(wl: dict, budget_s: float = 12.0) -> dict:
+def _oracle_ks_rate(n_points: int, threads: int, budget_s: float) -> tuple:
+    """(G point-updates/s, timesteps, seconds) of the CPU oracle's classic KS
+    from the initial state, about budget_s of work."""
     import oracle as O
-    spec = I.ks_spec(wl["n_points"])
+    spec = I.ks_spec(n_points)
     u = I.initial_state(spec)
     prob = O.OracleProblem(O.KS, O.PERIODIC, spec.n_points, spec.dx, spec.dt)
     t0 = time.perf_counter()
-    O.classic(prob, u, 4)
-    probe = max(time.perf_counter() - t0, 1e-3) / 4
+    O.classic(prob, u, 2, threads=threads)
+    probe = max(time.perf_counter() - t0, 1e-3) / 2
     steps = max(4, int(budget_s / probe))
     t0 = time.perf_counter()
-    O.classic(prob, u, steps)
+    O.classic(prob, u, steps, threads=threads)
     el = time.perf_counter() - t0
-    return {"value": spec.n_points * steps / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "host": _host_cpu(),
-            "sample": f"KS N=2^20 FP64 classic oracle, {steps} timesteps from the initial state "
-                      f"(of the workload's {wl['steps']}), single thread, {el:.1f} s"}
+    return spec.n_points * steps / el / 1e9, steps, el
+
+
+def cpu_oracle_rate(wl: dict, budget_s: float = 8.0) -> dict:
+    """The CPU oracle as it stands, on the host: its OpenMP build on all cores
+    (the baseline) and its single-threaded build beside it."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    used = O.omp_threads(cores)
+    v_all, st_all, el_all = _oracle_ks_rate(wl["n_points"], used, budget_s)
+    v_one, st_one, el_one = _oracle_ks_rate(wl["n_points"], 1, budget_s)
+    return {"value": v_all, "unit": UNIT, "cores": used, "kind": "oracle", "host": _host_cpu(),
+            "sample": f"KS N=2^20 FP64 classic oracle (OpenMP build, {used} threads), {st_all} timesteps from "
+                      f"the initial state (of the workload's {wl['steps']}), {el_all:.1f} s",
+            "single_thread": {"value": v_one, "unit": UNIT, "cores": 1,
+                              "sample": f"the single-threaded oracle, {st_one} timesteps, {el_one:.1f} s"}}
 
 
 def run_reference(args, wl):
+    """The reference arm: the CPU oracle (OpenMP build) on all host cores,
+    for the same metric and workload; rank 0 alone."""
     world, rank, _ = _dist_init()
     if rank != 0:
         return
@@ -215,16 +262,17 @@ def run_reference(args, wl):
     spec = I.ks_spec(wl["n_points"])
     u0 = I.initial_state(spec)
     prob = O.OracleProblem(O.KS, O.PERIODIC, spec.n_points, spec.dx, spec.dt)
+    cores = O.omp_threads(os.cpu_count() or 1)
     sample_steps = 16
     for _ in range(args.warmup):
-        O.classic(prob, u0.copy(), sample_steps)
+        O.classic(prob, u0.copy(), sample_steps, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.classic(prob, u0.copy(), sample_steps)
+        O.classic(prob, u0.copy(), sample_steps, threads=cores)
     el = time.perf_counter() - t0
     value = spec.n_points * sample_steps * args.steps / el / 1e9
-    sample = (f"each step: KS N=2^20 FP64 classic oracle for {sample_steps} of the workload's "
-              f"{wl['steps']} timesteps, single thread")
+    sample = (f"each step: KS N=2^20 FP64 classic oracle (OpenMP build) for {sample_steps} of the workload's "
+              f"{wl['steps']} timesteps, {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
@@ -232,13 +280,12 @@ def run_reference(args, wl):
         "data": "synthetic",
         "config": {"workload": WORKLOAD.format("FP64"), "n_points": wl["n_points"],
                    "timesteps": wl["steps"], "sample_timesteps": sample_steps, "scheme": "classic (CPU oracle)",
-                   "parallelism": "one host thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                   "parallelism": f"{cores} host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                          "host": _host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
 
 
 # ---------------------------------------------------------------------------
@@ -249,23 +296,45 @@ def _spec_ic(eq: str, N: int, dtype=np.float64):
     return spec, I.initial_state(spec, dtype)
 
 
-def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), width: int = 0,
-                threads: int = 0) -> dict:
-    """4096 independent heat + KS instances, N log-uniform 2^10..2^16, steps
-    U(10^3, 10^4), one persistent launch per precision replayed from a CUDA
-    graph, scheme (swept or classic) and width autotuned per (equation,
-    power-of-two N) bucket (or every instance swept at node width `width`,
-    halved until it divides N); against advancing a sample of the same
-    instances one by one."""
-    import math
-    import torch
-    from paper_1705_03162_gb300 import swept as S
+def batched_cases(count: int = 4096, seed: int = 20170509):
+    """(equation, N, timesteps) of the batched workload: heat and KS
+    alternating, N log-uniform on [2^10, 2^16] (any integer), timesteps
+    uniform on [10^3, 10^4]."""
     rng = np.random.default_rng(seed)
     cases = []
     for i in range(count):
-        N = max(1024, int(round(2 ** rng.uniform(10, 16) / 128)) * 128)
+        N = int(round(2 ** rng.uniform(10, 16)))
         cases.append(("heat" if i % 2 == 0 else "ks", N, int(rng.integers(1000, 10001))))
-    out = {"instances": count, "workload": "heat+KS, N log-uniform 2^10..2^16, steps U(1e3,1e4)"}
+    return cases
+
+
+def fit_width(eq: str, N: int, n: int) -> int:
+    """A tuned power-of-two node width for a bucket, halved until it is valid
+    for N: it divides N, or leaves at least two nodes (the remainder widens
+    some of them)."""
+    step = 4 if eq == "heat" else 8
+    while n > step and not (N % n == 0 or N // n >= 2):
+        n //= 2
+    return n
+
+
+def bucket(N: int) -> int:
+    import math
+    return min(max(int(round(math.log2(N))), 10), 16)
+
+
+def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), width: int = 0,
+                threads: int = 0) -> dict:
+    """4096 independent heat + KS instances (batched_cases), one persistent
+    launch per precision replayed from a CUDA graph, scheme (swept or
+    classic) and node width autotuned per (equation, nearest power-of-two N)
+    bucket (or every instance swept at node width `width`); against advancing
+    a sample of the same instances one by one, whose results must equal the
+    batch's bit for bit."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    cases = batched_cases(count, seed)
+    out = {"instances": count, "workload": "heat+KS, N log-uniform 2^10..2^16 (any integer), steps U(1e3,1e4)"}
     for dtype in dtypes:
         npdt = np.float64 if dtype == "f64" else np.float32
         t0 = time.perf_counter()
@@ -277,16 +346,13 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
                                                                             dtype=dtype)
         tune_s = time.perf_counter() - t0
         stream = torch.cuda.Stream()
-        probs, schemes, widths = [], [], []
+        probs, schemes, widths, inputs = [], [], [], []
         for eq, N, steps in cases:
             spec, u0 = _spec_ic(eq, N, npdt)
+            inputs.append((spec, u0))
             probs.append(S.Problem(spec, u0, dtype, stream=stream))
-            scheme, n = tuned[(eq, min(max(int(round(math.log2(N))), 10), 16))]
-            if scheme == "swept":
-                while N % n:
-                    n //= 2
-            else:
-                n = min(n, N)
+            scheme, n = tuned[(eq, bucket(N))]
+            n = fit_width(eq, N, n) if scheme == "swept" else min(n, N)
             schemes.append(scheme)
             widths.append(n)
         steps = [c[2] for c in cases]
@@ -306,53 +372,95 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
             bt.synchronize()
             ms = ev0.elapsed_time(ev1)
             launches = bt.kernel_launches() - l0
+        # a sample advanced one problem at a time (the first advance timed),
+        # three advances like the batch's: the results must be the batch's bits
         sample = range(min(32, count))
         su = float(sum(cases[i][1] * cases[i][2] for i in sample))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        solo_s, mismatches = 0.0, 0
         for i in sample:
-            probs[i].advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
-        torch.cuda.synchronize()
-        per_inst = su / (time.perf_counter() - t0) / 1e9
+            spec, u0 = inputs[i]
+            with S.Problem(spec, u0, dtype) as q:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
+                q.synchronize()
+                solo_s += time.perf_counter() - t0
+                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
+                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
+                mismatches += int(not np.array_equal(q.read(), probs[i].read()))
         for p in probs:
             p.close()
+        if mismatches:
+            raise AssertionError(f"batched {dtype}: {mismatches} sampled instances differ from solo advances")
+        eqs = [c[0] for c in cases]
+        flops = sum(c[1] * c[2] * op_count(c[0]) for c in cases)
+        ops = sum(c[1] * c[2] * op_count(c[0], "ops") for c in cases)
+        peak = FP32_PEAK_TFLOPS if dtype == "f32" else FP64_PEAK_TFLOPS
         out[dtype] = {"value": upd / ms / 1e6, "unit": UNIT, "ms": ms, "kernel_launches": launches,
                       "launch": "persistent kernel replayed from a CUDA graph",
-                      "per_instance_value": per_inst, "autotune_s": tune_s,
+                      "per_instance_value": su / solo_s / 1e9, "autotune_s": tune_s,
+                      "swept_instances": sum(1 for x in schemes if x == "swept"),
+                      "instances_with_wider_nodes": sum(1 for (e, N, _), sc, n in zip(cases, schemes, widths)
+                                                        if sc == "swept" and N % n),
+                      "sample_equals_solo_bitwise": f"{len(sample)} of {count} instances",
+                      "roofline": {"bound": "alu", "achieved": flops / ms / 1e9, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": flops / ms / 1e9 / peak, "pipe_ops_frac": ops / ms / 1e9 / (peak / 2),
+                                   "flops": f"heat {op_count('heat'):g}, KS {op_count('ks'):g} per update "
+                                            f"({eqs.count('heat')} heat, {eqs.count('ks')} KS)",
+                                   "peak_note": f"measured {'FP32' if dtype == 'f32' else 'FP64'} pipe"},
                       "tuned": {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}}
     return out
 
 
-def _trace(count: int, lam: float, seed: int):
+def served_requests(count: int, seed: int, steps_lo: int = 100, steps_hi: int = 1000):
+    """(unit-rate arrival gap, equation, N, timesteps) of the served mix:
+    heat, KS and Euler with equal probability, N log-uniform on [2^10, 2^20]
+    (any integer), timesteps uniform on [steps_lo, steps_hi]; the arrival
+    times of a trace at rate lam are the cumulative gaps / lam."""
     rng = np.random.default_rng(seed)
-    t, reqs = 0.0, []
-    for i in range(count):
-        t += rng.exponential(1.0 / lam)
+    out = []
+    for _ in range(count):
+        gap = float(rng.exponential(1.0))
         eq = ("heat", "ks", "euler")[int(rng.integers(0, 3))]
-        N = max(1024, int(round(2 ** rng.uniform(10, 20) / 1024)) * 1024)
-        reqs.append((t, eq, N, int(rng.integers(1000, 10001))))
+        N = int(round(2 ** rng.uniform(10, 20)))
+        out.append((gap, eq, N, int(rng.integers(steps_lo, steps_hi + 1))))
+    return out
+
+
+def _trace(count: int, lam: float, seed: int):
+    """(arrival time, equation, N, timesteps) of a Poisson trace at rate lam."""
+    t, reqs = 0.0, []
+    for gap, eq, N, st in served_requests(count, seed):
+        t += gap / lam
+        reqs.append((t, eq, N, st))
     return reqs
 
 
 def _percentiles(lat):
     lat = np.sort(np.asarray(lat))
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "mean_s": float(lat.mean()), "max_s": float(lat.max())}
+            "mean_s": float(lat.mean()), "max_s": float(lat.max()), "samples": int(lat.size)}
 
 
-def run_served(count: int, lam: float, seed: int, budget: int, baseline: bool = True) -> dict:
-    """Poisson arrivals of mixed heat / KS / Euler solves (FP64) served with
-    continuous batching, and the same trace solved one request at a time."""
+def fifo_latencies(arrivals, service):
+    """Latency of each request of a single FIFO server: it starts when it has
+    arrived and the previous request has finished, and takes its own
+    service time."""
+    t, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        start = max(a, t)
+        t = start + s
+        lat.append(t - a)
+    return lat
+
+
+def _serve(reqs, inputs, budget):
+    """Submit reqs (arrival, eq, N, steps) at their arrival times to a server
+    with continuous batching; latencies, span and server statistics."""
     import threading
-    import torch
     from paper_1705_03162_gb300 import swept as S
-    reqs = _trace(count, lam, seed)
-    inputs = [_spec_ic(eq, N) for _, eq, N, _ in reqs]
-    upd = float(sum(N * st for _, _, N, st in reqs))
-    res = {"requests": count, "lambda_per_s": lam, "hbm_budget_bytes": budget,
-           "mix": "heat/KS/Euler uniform, N log-uniform 2^10..2^20, steps U(1e3,1e4), FP64"}
     with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=5.0) as srv:
-        ids = [None] * count
+        ids = [None] * len(reqs)
         t_start = time.perf_counter()
 
         def feed():
@@ -369,29 +477,64 @@ def run_served(count: int, lam: float, seed: int, budget: int, baseline: bool = 
         lat = [srv.wait(i)[1] for i in ids]
         span = time.perf_counter() - t_start
         stats = srv.stats()
-    res["served"] = dict(_percentiles(lat), throughput=upd / span / 1e9, unit=UNIT,
-                         rounds=stats["rounds"], kernel_launches=stats["kernel_launches"])
-    if baseline:
-        lat_b = []
-        t_start = time.perf_counter()
-        for i, (t_arr, eq, N, st) in enumerate(reqs):
-            d = t_start + t_arr - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            spec, u0 = inputs[i]
-            with S.Problem(spec, u0) as p:
-                p.advance(st, "swept")
-                p.read()
-            lat_b.append(time.perf_counter() - (t_start + t_arr))
-        span_b = time.perf_counter() - t_start
-        res["per_instance"] = dict(_percentiles(lat_b), throughput=upd / span_b / 1e9, unit=UNIT)
+    return lat, span, stats
+
+
+def run_served(count: int = 1000, seed: int = 20170509, budget: int = 1 << 30) -> dict:
+    """Serving with continuous batching against one request at a time.
+
+    One request set (served_requests, FP64) at three offered loads: an
+    overload trace (lam = 2000/s), whose completion rate is the server's
+    capacity C, then Poisson traces at 0.95 C and 0.7 C (the same arrival
+    pattern, rescaled).  The per-instance baseline is a FIFO queue over each
+    request's own solo solve (create, advance with the library default, read
+    back), timed once on the host clock and replayed against every trace."""
+    from paper_1705_03162_gb300 import swept as S
+    base = served_requests(count, seed)
+    inputs = [_spec_ic(eq, N) for _, eq, N, _ in base]
+    upd = float(sum(N * st for _, _, N, st in base))
+    unit_arrivals = np.cumsum([g for g, _, _, _ in base])
+    res = {"requests": count, "hbm_budget_bytes": budget,
+           "mix": "heat/KS/Euler uniform, N log-uniform 2^10..2^20 (any integer), steps U(1e2,1e3), FP64",
+           "per_instance_baseline": "FIFO over each request's measured solo solve (create, advance, read)",
+           "loads": []}
+
+    def trace(lam):
+        return [(float(a / lam), eq, N, st) for a, (_, eq, N, st) in zip(unit_arrivals, base)]
+
+    # per-instance service times, one solve at a time
+    service = []
+    for (_, eq, N, st), (spec, u0) in zip(base, inputs):
+        t0 = time.perf_counter()
+        with S.Problem(spec, u0) as p:
+            p.advance(st, "swept")
+            p.read()
+        service.append(time.perf_counter() - t0)
+    res["per_instance_capacity_req_per_s"] = count / sum(service)
+    lam, cap = 2000.0, None
+    for label, frac in (("overload", None), ("0.95 of capacity", 0.95), ("0.7 of capacity", 0.7)):
+        if frac is not None:
+            lam = frac * cap
+        reqs = trace(lam)
+        lat, span, stats = _serve(reqs, inputs, budget)
+        if cap is None:
+            cap = count / span
+            res["capacity_req_per_s"] = cap
+        lat_b = fifo_latencies([r[0] for r in reqs], service)
+        span_b = max(r[0] + l for r, l in zip(reqs, lat_b))
+        res["loads"].append({
+            "label": label, "lambda_per_s": lam, "offered_load": lam / cap,
+            "served": dict(_percentiles(lat), throughput=upd / span / 1e9, unit=UNIT, rounds=stats["rounds"],
+                           kernel_launches=stats["kernel_launches"]),
+            "per_instance": dict(_percentiles(lat_b), throughput=upd / span_b / 1e9, unit=UNIT)})
     return res
 
 
 def other_configs() -> dict:
     """The heat configuration (N = 1024, r = 0.25, 4096 steps) and the Sod
     tube at N = 2^20 (4096 steps, dt/dx = 0.2): swept against classic, FP64,
-    device-timed.  Heat reports both swept forms, Shared (64-point nodes, CUDA
+    device-timed, with the swept result checked bit for bit against the
+    classic one.  Heat reports both swept forms, Shared (64-point nodes, CUDA
     graph) and the paper's Register variant (32-point warp nodes, graph), and
     the faster as `swept`."""
     import torch
@@ -401,16 +544,29 @@ def other_configs() -> dict:
                                ("Sod Euler N=2^20 4096 steps n=512 dataflow", "euler", 1 << 20, 4096)):
         spec, u0 = _spec_ic(eq, N)
         u0d = torch.from_numpy(u0).cuda()
-        rec = {}
+        rec, results = {}, {}
         with S.Problem(spec, u0d) as p:
             if eq == "heat":
-                rec["swept_shared_n64_graph"] = N * steps / _time_solve(p, u0d, steps, "swept", 64, "graph") / 1e9
-                rec["swept_register_graph"] = N * steps / _time_solve(p, u0d, steps, "swept", 32, "register") / 1e9
-                rec["swept"] = max(rec["swept_shared_n64_graph"], rec["swept_register_graph"])
+                t_sh = _time_solve(p, u0d, steps, "swept", 64, "graph")
+                results["swept_shared"] = p.read()
+                t_reg = _time_solve(p, u0d, steps, "swept", 32, "register")
+                results["swept_register"] = p.read()
+                rec["swept_shared_n64_graph"] = N * steps / t_sh / 1e9
+                rec["swept_register_graph"] = N * steps / t_reg / 1e9
+                t_sw = min(t_sh, t_reg)
             else:
-                rec["swept"] = N * steps / _time_solve(p, u0d, steps, "swept", 512, "persistent") / 1e9
-            rec["classic_graph"] = N * steps / _time_solve(p, u0d, steps, "classic", launch="graph") / 1e9
-        rec.update(unit=UNIT, swept_speedup=rec["swept"] / rec["classic_graph"])
+                t_sw = _time_solve(p, u0d, steps, "swept", 512, "persistent")
+                results["swept"] = p.read()
+            rec["swept"] = N * steps / t_sw / 1e9
+            t_cl = _time_solve(p, u0d, steps, "classic", launch="graph")
+            classic = p.read()
+            rec["classic_graph"] = N * steps / t_cl / 1e9
+        for k, v in results.items():
+            if not np.array_equal(v, classic):
+                raise AssertionError(f"{name}: {k} differs from classic")
+        rec.update(unit=UNIT, swept_speedup=rec["swept"] / rec["classic_graph"],
+                   swept_equals_classic_bitwise=True,
+                   roofline=alu_roofline(float(N) * steps, t_sw, eq, "f64"))
         out[name] = rec
     return out
 
@@ -431,6 +587,56 @@ def fp32_error() -> dict:
             got = p.read().astype(np.float64)
         out[name] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     return out
+
+
+def sweep_line(steps: int = 500) -> dict:
+    """Swept at the library default (SWP_LAUNCH_AUTO and the default width)
+    against classic replayed as a CUDA graph, heat and KS FP64 at
+    N = 2^11..2^20 (the paper's size range, Section 6), with each one's
+    fraction of the FP64 pipe."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    pts = []
+    for eq in ("heat", "ks"):
+        for e in range(11, 21):
+            N = 1 << e
+            spec, u0 = _spec_ic(eq, N)
+            u0d = torch.from_numpy(u0).cuda()
+            with S.Problem(spec, u0d) as p:
+                t_cl = _time_solve(p, u0d, steps, "classic", launch="graph")
+                t_sw = _time_solve(p, u0d, steps, "swept", 0, "auto")
+            pts.append({"eq": eq, "n_points": N, "classic_graph": N * steps / t_cl / 1e9,
+                        "swept": N * steps / t_sw / 1e9, "speedup": t_cl / t_sw,
+                        "swept_frac": alu_roofline(float(N) * steps, t_sw, eq, "f64")["frac"],
+                        "classic_frac": alu_roofline(float(N) * steps, t_cl, eq, "f64")["frac"]})
+    return {"timesteps": steps, "dtype": "f64", "unit": UNIT,
+            "swept": "library default (SWP_LAUNCH_AUTO, default node width)", "classic": "CUDA graph",
+            "frac": "algorithmic flops / time / measured FP64 pipe", "points": pts,
+            "swept_beats_classic_at": f"{sum(1 for q in pts if q['speedup'] > 1)} of {len(pts)} sizes"}
+
+
+def bandwidth_line(steps: int = 200) -> dict:
+    """Classic FP32 heat and KS at N = 2^26 (arrays far beyond L2), replayed as
+    a CUDA graph: achieved algorithmic HBM bandwidth against the measured copy
+    peak (heat reads and writes one value per update, 8 B; a KS timestep
+    reads u, writes the predictor, reads it and u and writes u, 20 B)."""
+    import torch
+    from paper_1705_03162_gb300 import swept as S
+    peak, src = hbm_peak()
+    N = 1 << 26
+    out = {"n_points": N, "dtype": "f32", "hbm_peak_gbs": peak, "peak_source": src, "lines": []}
+    for eq, bytes_per_update, st in (("heat", 8, steps), ("ks", 20, steps // 2)):
+        spec, u0 = _spec_ic(eq, N, np.float32)
+        u0d = torch.from_numpy(u0).cuda()
+        with S.Problem(spec, u0d, "f32") as p:
+            t = _time_solve(p, u0d, st, "classic", launch="graph")
+        gbs = bytes_per_update * N * st / t / 1e9
+        out["lines"].append({"eq": eq, "timesteps": st, "value": N * st / t / 1e9, "unit": UNIT,
+                             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                          "frac": gbs / peak, "bytes_per_update": bytes_per_update}})
+        del u0d
+    return out
+
 
 # ---------------------------------------------------------------------------
 # GPU arm
@@ -492,12 +698,16 @@ def run_gpu(args, wl):
     torch.cuda.synchronize()
     dist.barrier()
     t_swept = dist.max(t_swept)
+    swept_result = prob.read()     # outside the timed regions
     l1 = prob.kernel_launches()
     t_classic = timed("classic", args.steps)
     launches_classic = prob.kernel_launches() - l1
     torch.cuda.synchronize()
     dist.barrier()
     t_classic = dist.max(t_classic)
+    classic_result = prob.read()
+    if not np.array_equal(swept_result, classic_result):
+        raise AssertionError("the timed swept solve differs from the classic solve")
     # classic with its launch sequence as a CUDA graph (captured in warm-up)
     prob.write(u0_dev)
     prob.advance(steps, "classic", launch="graph")
@@ -528,6 +738,7 @@ def run_gpu(args, wl):
         prob.read(pinned_out)
     t_e2e = dist.max(time.perf_counter() - t0)
     prob.close()
+    del flush
 
     upd = float(N) * steps * args.steps * world
     value = upd / t_swept / 1e9
@@ -535,19 +746,18 @@ def run_gpu(args, wl):
     classic_graph_value = upd / t_classic_graph / 1e9
     e2e_value = upd / t_e2e / 1e9
 
-    # roofline of the dominant kernel (the swept phase kernel, FP64-pipe bound)
+    # roofline of the dominant kernel (the dataflow kernel, FP64-pipe bound):
+    # algorithmic flops of one launch / its average duration
     launches_per_solve = launches_swept / args.steps
     avg_launch_s = t_swept / args.steps / launches_per_solve
-    flops_per_launch = float(N) * steps * KS_FLOPS_PER_UPDATE / launches_per_solve
-    achieved = flops_per_launch / avg_launch_s / 1e12
-    ops_rate = float(N) * steps * args.steps * KS_FP64_OPS_PER_UPDATE / t_swept / 1e12
-    peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+    roof = alu_roofline(float(N) * steps / launches_per_solve, avg_launch_s, "ks", wl["dtype"])
     key = (f"{KERNEL_OF_LAUNCH[wl['launch']]}<{'float' if f32 else 'double'},KS> "
            f"n={wl['points_per_block']} threads={wl['threads']}")
     traffic = None
     rec = NCU_TRAFFIC.get(key)
     if rec and rec.get("src") == _kernel_src_hash():
         traffic = rec["bytes_per_launch"]
+    roof.update(traffic=traffic, kernel=key)
 
     if rank != 0:
         dist.close()
@@ -566,38 +776,34 @@ def run_gpu(args, wl):
                     "swept_speedup": classic_value and value / classic_value,
                     "graph_value": classic_graph_value,
                     "swept_speedup_vs_graph": value / classic_graph_value},
+        "parity": {"swept_equals_classic_bitwise": True, "checked": "final states of the timed solves"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(u0_host.nbytes),
                 "d2h_bytes_per_step": int(u0_host.nbytes)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": key, "flops_per_update": KS_FLOPS_PER_UPDATE,
-                     ("fp32_ops_per_update" if f32 else "fp64_ops_per_update"): KS_FP64_OPS_PER_UPDATE,
-                     ("fp32_pipe_frac" if f32 else "fp64_pipe_frac"): ops_rate / (peak / 2),
-                     "peak_note": ("FP32 pipe derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz" if f32 else
-                                   "FP64 pipe derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz")},
+        "roofline": roof,
         "gpu_launches": int(launches_swept),
         "clocks": clk,
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(wl)
     if world == 1 and not args.no_extras:
-        line["served"] = {
-            "lambda_2000": run_served(48, 2000.0, 20170509, 1 << 30),
-            "below_saturation": run_served(24, 2.5, 20170510, 1 << 30, baseline=True),
-        }
-        line["batched"] = run_batched()
-        line["fp32_rel_error_vs_fp64_oracle"] = fp32_error()
+        line["sweep"] = sweep_line()
+        line["bandwidth"] = bandwidth_line()
         line["other_configs"] = other_configs()
+        line["fp32_rel_error_vs_fp64_oracle"] = fp32_error()
+        line["batched"] = run_batched()
+        line["served"] = run_served()
     print(json.dumps(line), flush=True)
     dist.close()
 
 
-
 # ---------------------------------------------------------------------------
-# optional modes: size sweep and classic bandwidth
+# optional modes: full size sweep (every width and launch), Sod sweep
 # ---------------------------------------------------------------------------
 def _time_solve(prob, u0d, steps, scheme, n=0, launch="per_phase", threads=0, reps=2):
+    """Best of reps device-timed solves from u0d (after a short warm-up that
+    also captures any graph); the state is the last solve's result."""
     import torch
+    prob.write(u0d)
     prob.advance(min(steps, 20), scheme, n, launch, threads)
     torch.cuda.synchronize()
     best = float("inf")
@@ -613,9 +819,9 @@ def _time_solve(prob, u0d, steps, scheme, n=0, launch="per_phase", threads=0, re
 
 
 def run_sweep(steps: int = 2000):
-    """Swept (shared, best node width and launch: per-phase, graph or dataflow),
-    Register variant and classic (CUDA graph) for heat and KS at N = 2^11..2^20,
-    FP64: one JSON line each."""
+    """Swept (shared, every node width and launch: per-phase, graph or
+    dataflow), the library default, the Register variant and classic (CUDA
+    graph) for heat and KS at N = 2^11..2^20, FP64: one JSON line each."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     for eq in ("ks", "heat"):
@@ -623,20 +829,23 @@ def run_sweep(steps: int = 2000):
             N = 1 << e
             spec, u0 = _spec_ic(eq, N)
             u0d = torch.from_numpy(u0).cuda()
+            runs = []
             with S.Problem(spec, u0d) as p:
                 classic = N * steps / _time_solve(p, u0d, steps, "classic", launch="graph") / 1e9
                 reg = N * steps / _time_solve(p, u0d, steps, "swept", 0, "register", 64) / 1e9
+                auto = N * steps / _time_solve(p, u0d, steps, "swept", 0, "auto") / 1e9
                 best, cfg = 0.0, None
                 for n in (64, 128, 256, 512, 1024):
                     if N % n or N // n < 2:
                         continue
                     for launch in ("per_phase", "graph", "persistent"):
                         r = N * steps / _time_solve(p, u0d, steps, "swept", n, launch) / 1e9
+                        runs.append((n, launch, round(r, 3)))
                         if r > best:
                             best, cfg = r, {"points_per_block": n, "launch": launch}
             print(json.dumps({"sweep": eq, "n_points": N, "timesteps": steps, "dtype": "f64", "unit": UNIT,
-                              "classic_graph": classic, "swept": best, "swept_config": cfg,
-                              "register": reg, "swept_speedup": best / classic}), flush=True)
+                              "classic_graph": classic, "swept": best, "swept_config": cfg, "auto": auto,
+                              "register": reg, "swept_speedup": best / classic, "runs": runs}), flush=True)
 
 
 def run_sod(exps, steps: int, widths=None, threads=None):
@@ -667,30 +876,6 @@ def run_sod(exps, steps: int, widths=None, threads=None):
               flush=True)
 
 
-def run_bandwidth(steps: int = 200):
-    """Classic FP32 heat and KS at N = 2^26 (arrays far beyond L2): achieved
-    algorithmic HBM bandwidth against the measured copy peak."""
-    import torch
-    from paper_1705_03162_gb300 import swept as S
-    peak = 6790.3
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak = float(json.load(f)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        pass
-    N = 1 << 26
-    for eq, bytes_per_update in (("heat", 8), ("ks", 20)):
-        spec, u0 = _spec_ic(eq, N, np.float32)
-        u0d = torch.from_numpy(u0).cuda()
-        with S.Problem(spec, u0d, "f32") as p:
-            t = _time_solve(p, u0d, steps if eq == "heat" else steps // 2, "classic", launch="graph")
-        st = steps if eq == "heat" else steps // 2
-        gbs = bytes_per_update * N * st / t / 1e9
-        print(json.dumps({"bandwidth": f"classic {eq} FP32 N=2^26", "timesteps": st,
-                          "value": N * st / t / 1e9, "unit": UNIT, "algorithmic_gbs": gbs,
-                          "bytes_per_update": bytes_per_update, "hbm_peak_gbs": peak,
-                          "frac": gbs / peak}), flush=True)
-
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -704,8 +889,8 @@ def main():
     ap.add_argument("--dtype", choices=["f64", "f32"], default=DEFAULT_WORKLOAD["dtype"],
                     help="precision of the timed KS workload (FP64 is the benchmark; FP32 is the variant)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep", action="store_true", help="print the per-size sweep lines instead")
-    ap.add_argument("--bandwidth", action="store_true", help="print the classic FP32 bandwidth lines instead")
+    ap.add_argument("--sweep", action="store_true", help="print the full per-size sweep lines instead")
+    ap.add_argument("--bandwidth", action="store_true", help="print the classic FP32 bandwidth line instead")
     ap.add_argument("--sod", type=int, nargs="*", metavar="LOG2N",
                     help="print Sod swept-vs-classic lines for N = 2^LOG2N (default 11 14 17 20) instead; "
                          "--timesteps defaults to 4096 here, and --points-per-block / --threads, when given, "
@@ -714,8 +899,9 @@ def main():
                     help="print the batched heat+KS line for COUNT instances in the --dtype precision instead; "
                          "--points-per-block, when given, replaces the autotuned widths, and --threads sets "
                          "the batch's block size")
+    ap.add_argument("--served", type=int, metavar="COUNT", help="print the served line for COUNT requests instead")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the served, batched and FP32-error measurements")
+                    help="skip the sweep, bandwidth, other-configuration, batched, served and FP32-error lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -729,26 +915,26 @@ def main():
             wl[key] = val
     if args.impl == "reference":
         run_reference(args, wl)
-    elif args.batched is not None:
+        return
+    if args.batched is not None or args.sod is not None or args.sweep or args.bandwidth or args.served:
         from paper_1705_03162_gb300 import swept as S
         S.load_library()
+    if args.batched is not None:
         if args.batched < 1:
             ap.error("--batched needs COUNT >= 1")
         print(json.dumps({"batched": run_batched(args.batched, dtypes=(args.dtype,),
                                                  width=args.points_per_block or 0, threads=args.threads or 0)}))
     elif args.sod is not None:
-        from paper_1705_03162_gb300 import swept as S
-        S.load_library()
         run_sod(args.sod or [11, 14, 17, 20], args.timesteps or 4096,
                 [args.points_per_block] if args.points_per_block else None,
                 [args.threads] if args.threads else None)
+    elif args.served:
+        print(json.dumps({"served": run_served(args.served)}))
     elif args.sweep or args.bandwidth:
-        from paper_1705_03162_gb300 import swept as S
-        S.load_library()
         if args.sweep:
             run_sweep()
         if args.bandwidth:
-            run_bandwidth()
+            print(json.dumps({"bandwidth": bandwidth_line()}))
     else:
         run_gpu(args, wl)
 

@@ -197,8 +197,8 @@ swp_status check_width(const swp_problem* p, int n)
 
 // Default node width, from the widths measured fastest on GB300 for single
 // problems: about N / 1024 points for heat and KS (N / 512 in the persistent
-// dataflow launch; at least 64 and 128, at most 1024) and N / 256 for Euler
-// (64 to 512).  The nearest width down to half the target that divides N and
+// dataflow launch; at least 128, at most 1024) and N / 256 for Euler (64 to
+// 512).  The nearest width down to half the target that divides N and
 // is a multiple of 4 rad; else the target itself (rounded down to a multiple
 // of 4 rad), whose remainder widens some nodes; 0 when N is too small for
 // any (fewer than two nodes of 4 rad points).
@@ -206,7 +206,7 @@ int default_width(const swp_problem* p, bool dataflow = false)
 {
     const int step = 4 * p->rad;
     const bool euler = p->desc.eq == SWP_EULER;
-    const int lo = (p->desc.eq == SWP_HEAT || euler) ? 64 : 128;
+    const int lo = euler ? 64 : 128;
     const int cap = euler ? 512 : 1024;
     int64_t target = p->N / (euler ? 256 : (dataflow ? 512 : 1024));
     if (target < lo) target = lo;

@@ -35,8 +35,41 @@ def test_served_trace_is_seeded_and_ordered():
     assert times == sorted(times) and times[0] > 0
     for _, eq, N, steps in t1:
         assert eq in ("heat", "ks", "euler")
-        assert N % 1024 == 0 and 1024 <= N <= (1 << 20)
-        assert 1000 <= steps <= 10000
+        assert 1024 <= N <= (1 << 20)
+        assert 100 <= steps <= 1000
+    assert any(N % 1024 for _, _, N, _ in t1)   # any integer N, not rounded
+    # the same request set at another rate: the arrival pattern rescaled
+    t3 = bench._trace(48, 500.0, 20170509)
+    assert [r[1:] for r in t3] == [r[1:] for r in t1]
+    assert np.allclose([r[0] for r in t3], [4 * r[0] for r in t1])
+
+
+def test_fifo_latencies():
+    # arrivals 0, 1, 1.5; service 2, 1, 1: the second waits for the first
+    lat = bench.fifo_latencies([0.0, 1.0, 1.5], [2.0, 1.0, 1.0])
+    assert lat == [2.0, 2.0, 2.5]
+    assert bench.fifo_latencies([0.0, 10.0], [1.0, 1.0]) == [1.0, 1.0]
+
+
+def test_batched_cases_and_widths():
+    cases = bench.batched_cases(512)
+    assert cases == bench.batched_cases(512)
+    assert [c[0] for c in cases[:4]] == ["heat", "ks", "heat", "ks"]
+    assert all(1024 <= N <= 65536 and 1000 <= st <= 10000 for _, N, st in cases)
+    assert any(N % 128 for _, N, _ in cases)
+    for eq, N, _ in cases:
+        n = bench.fit_width(eq, N, 1024)
+        assert N % n == 0 or N // n >= 2
+        assert n % (4 if eq == "heat" else 8) == 0
+    assert bench.bucket(1024) == 10 and bench.bucket(65536) == 16 and bench.bucket(3000) == 12
+
+
+def test_op_counts_table():
+    assert bench.op_count("ks") == 22 and bench.op_count("ks", "ops") == 14
+    assert bench.op_count("heat") == 5 and bench.op_count("heat", "ops") == 3
+    assert 100 < bench.op_count("euler", "ops") < 200
+    r = bench.alu_roofline(1e10, 1.0, "ks", "f64")
+    assert abs(r["achieved"] - 0.22) < 1e-12 and r["peak"] == bench.FP64_PEAK_TFLOPS
 
 
 def test_percentiles():
