@@ -994,10 +994,12 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     w.flags = t.flags;
     w.wait_limit_ns = wait_limit ? wait_limit : b->wait_limit_ns;
     w.wait_offset = wait_offset;
-    bool reg = false;
-    for (const auto& it : items)
+    bool reg = false, cls = false;
+    for (const auto& it : items) {
         if (it.kind == BATCH_SWEPT && swept_reg_slots(it.p->desc.eq, it.s.n, threads, it.p->esize) > 0) reg = true;
-    int bps = swept_batch_blocks_per_sm<R>(mode, reg, smem, threads);
+        if (it.kind == BATCH_CLASSIC) cls = true;
+    }
+    int bps = swept_batch_blocks_per_sm<R>(mode, reg, cls, smem, threads);
     if (max_blocks_per_sm > 0 && bps > max_blocks_per_sm) bps = max_blocks_per_sm;
     if (bps <= 0) {
         if (graph) gnew.t.release();
@@ -1009,7 +1011,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
     if (!graph) {
         e = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->stream);
-        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->stream);
+        if (e == cudaSuccess) e = launch_swept_batch<R>(mode, reg, cls, dinsts, w, threads, (int)blocks, b->stream);
         if (e != cudaSuccess) return cuda_fail(e, "batch launch");
     } else {
         // the uploads above are ordinary stream work; the graph holds the rest
@@ -1026,7 +1028,7 @@ swp_status batch_group(swp_batch* b, const std::vector<BatchItem>& items, int mo
             cudaError_t e1 = cudaMemsetAsync(t.ctr, 0, sizeof(int) * (ntasks + 1), b->capture_stream);
             if (e1 == cudaSuccess)
                 e1 = cudaMemsetAsync(t.flags, 0, sizeof(uint32_t) * (size_t)flags, b->capture_stream);
-            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, reg, dinsts, w, threads, (int)blocks, b->capture_stream);
+            if (e1 == cudaSuccess) e1 = launch_swept_batch<R>(mode, reg, cls, dinsts, w, threads, (int)blocks, b->capture_stream);
             e = cudaStreamEndCapture(b->capture_stream, &cg);
             if (e1 != cudaSuccess) e = e1;
         }

@@ -93,13 +93,14 @@ struct BatchWork {
 // mode: HEAT for a heat / KS launch, EULER for an Euler launch.  reg: the
 // heat / KS launch runs its nodes' levels register-blocked where
 // swept_reg_slots allows (nodes next to non-periodic ends stay in shared
-// memory).
+// memory).  cls: the launch holds classic instances (else the kernel is the
+// one compiled without them).
 template <typename R>
-cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
-                               int blocks, cudaStream_t s);
+cudaError_t launch_swept_batch(int mode, bool reg, bool cls, const BatchInst<R>* insts, const BatchWork& w,
+                               int threads, int blocks, cudaStream_t s);
 
 template <typename R>
-int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads);
+int swept_batch_blocks_per_sm(int mode, bool reg, bool cls, size_t smem_bytes, int threads);
 
 // Slots per thread of the register-blocked swept levels for node width n and
 // block size threads (2, 4, 8 or, FP32, 16), or 0 when the levels run in

@@ -8,14 +8,15 @@
 //    resident on the device until it finishes;
 //  - rounds: an admitted request's whole solve is one swept plan (node width
 //    fixed at admission) run a few phases at a time, the open triangle
-//    edges staying in its rows between rounds.  Each round gives every
-//    active request an equal share of a target round time as credit
-//    (estimated FP64 work per point-update of its equation) and runs as many
-//    of its next phases as its credit pays for (deficit round robin), all in
-//    one batched launch per group (a round of one request below 2^17 points,
-//    or in FP32, runs as that request's per-phase launches, as swp_advance
-//    would run it alone); requests that arrive meanwhile join the next round,
-//    so new and in-flight work overlap on the device;
+//    edges staying in its rows between rounds.  A round runs every request
+//    whose remaining work (estimated FP64 work per point-update of its
+//    equation) fits in a target round time to its end, and the long ones
+//    first come, first served: the oldest for a round's worth of phases,
+//    younger ones beside it while the GPU has idle blocks.  All of it goes
+//    into one batched launch per group (a round of one request below 2^17
+//    points, or in FP32, runs as that request's per-phase launches, as
+//    swp_advance would run it alone); requests that arrive meanwhile join
+//    the next round, so new and in-flight work overlap on the device;
 //  - retirement: finished requests are copied back to host memory, their
 //    device memory is freed, and waiters are woken.
 // A request's phases are those of one swept advance of its whole step count,
@@ -57,7 +58,8 @@ struct Request {
     int n = 0;                           // node width of the request's swept plan (classic: chunk width)
     int kind = swp::BATCH_SWEPT;         // BATCH_CLASSIC when N is too small for any node width
     int64_t n_phases = 0, phase_next = 0;
-    double phase_cost = 0.0, credit = 0.0;   // estimated FP64 operations
+    double phase_cost = 0.0;             // estimated FP64 operations of one phase
+    int64_t width = 0;                   // nodes (classic: chunks) per phase
     int state = 0;                       // 0 pending, 1 active, 2 done
     swp_status status = SWP_OK;
     std::string error;                   // why it failed (handed to the waiter)
@@ -88,6 +90,7 @@ struct swp_server {
     cudaStream_t stream = nullptr;
     int device = 0;
     swp_batch* batch = nullptr;
+    int64_t width_cap = 608;   // nodes in flight that fill the GPU: 4 per SM
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     bool stop = false;
@@ -158,6 +161,8 @@ void swp_server::admit()
         }
         r->phase_cost = (double)r->desc.n_points * (double)r->steps_total * cost_per_update(r->desc) /
                         (double)r->n_phases;
+        r->width = r->kind == swp::BATCH_SWEPT ? r->desc.n_points / r->n
+                                               : (r->desc.n_points + r->n - 1) / r->n;
         r->bytes = need;
         in_use += need;
         r->u0.clear();
@@ -170,33 +175,48 @@ void swp_server::admit()
 
 swp_status swp_server::round()
 {
-    // called without mu: the active list only changes on this thread
-    const double budget_ops = cfg.round_target_ms * 1e-3 * 4.0e11;
-    const double share = budget_ops / (double)active.size();
+    // called without mu: the active list only changes on this thread.
+    // Requests are in arrival order (admission is first come, first served
+    // and retirement keeps the order).  A request whose remaining work fits in
+    // one round's budget (a small one) runs all its remaining phases now, so
+    // it never waits behind a long solve.  Longer ones run first come, first
+    // served: the oldest runs a round's budget of its phases, and younger ones
+    // join it only while the nodes of those already chosen leave blocks of the
+    // GPU idle (a narrow solve cannot fill the GPU by itself), each also with
+    // a round's budget.  A long solve therefore runs at nearly its solo speed
+    // and waits only for long solves that arrived before it.
+    // When every active request is long and none is pending, rounds are four
+    // times longer: fewer rounds, less host work between them, and a request
+    // arriving meanwhile waits at most one such round.
+    double budget_ops = cfg.round_target_ms * 1e-3 * 4.0e11;
+    bool all_long = true;
+    for (auto& rq : active)
+        if ((double)(rq->n_phases - rq->phase_next) * rq->phase_cost <= budget_ops) all_long = false;
+    bool idle_queue;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        idle_queue = pending.empty();
+    }
+    const double long_budget = all_long && idle_queue ? 4.0 * budget_ops : budget_ops;
     std::vector<swp::PhaseRange> ranges;
     std::vector<int64_t> take(active.size(), 0);
-    size_t richest = 0;
+    int64_t width = 0;   // nodes (or chunks) per phase of the long solves chosen
+    bool any_long = false;
     for (size_t i = 0; i < active.size(); ++i) {
         Request& r = *active[i];
-        r.credit += share;
-        if (r.credit / r.phase_cost > active[richest]->credit / active[richest]->phase_cost) richest = i;
-        take[i] = r.credit > 0.0 ? std::min<int64_t>((int64_t)(r.credit / r.phase_cost), r.n_phases - r.phase_next)
-                                 : 0;
-    }
-    bool any = false;
-    double assigned = 0.0;
-    for (size_t i = 0; i < active.size(); ++i) {
-        any = any || take[i] > 0;
-        assigned += (double)take[i] * active[i]->phase_cost;
-    }
-    if (!any) {   // every credit is short of a phase: run the closest one
-        take[richest] = 1;
-        assigned = active[richest]->phase_cost;
+        const int64_t left = r.n_phases - r.phase_next;
+        if ((double)left * r.phase_cost <= budget_ops) {
+            take[i] = left;
+            continue;
+        }
+        if (any_long && width >= width_cap) continue;
+        take[i] = std::min<int64_t>(left, std::max<int64_t>(1, (int64_t)(long_budget / r.phase_cost)));
+        width += r.width;
+        any_long = true;
     }
     for (size_t i = 0; i < active.size(); ++i) {
         if (take[i] <= 0) continue;
         Request& r = *active[i];
-        r.credit -= (double)take[i] * r.phase_cost;
         ranges.push_back(swp::PhaseRange{r.prob, r.n, r.steps_total, r.phase_next, r.phase_next + take[i], r.kind});
     }
     const int64_t l0 = swp_batch_kernel_launches(batch);
@@ -310,10 +330,13 @@ swp_status swp_server_create(const swp_server_config* cfg, void* cuda_stream, sw
     if (!s) return swp::set_error(SWP_ENOMEM, "host allocation failed");
     s->cfg = *cfg;
     s->stream = (cudaStream_t)cuda_stream;
-    if (cudaGetDevice(&s->device) != cudaSuccess) {
+    int sms = 0;
+    if (cudaGetDevice(&s->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
         delete s;
         return swp::set_error(SWP_EDEVICE, "no usable CUDA device");
     }
+    s->width_cap = 4 * (int64_t)sms;
     swp_status st = swp_batch_create(cuda_stream, &s->batch);
     if (st != SWP_OK) {
         delete s;

@@ -752,7 +752,10 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
 }
 
 // MODE HEAT: heat and KS instances (chosen per item); MODE EULER: Euler.
-template <typename R, int MODE, bool REG>
+// CLS: the launch holds classic instances too (their items are compiled in
+// only then, so that swept-only launches keep fewer registers: Euler 80
+// against 63 without).
+template <typename R, int MODE, bool REG, bool CLS>
 __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel(const BatchInst<R>* insts,
                                                                                 BatchWork w)
 {
@@ -784,7 +787,7 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
             // items of the previous phase this one reads: swept, the two
             // overlapping nodes; classic, the chunk and its neighbours
             int kl, km, kr;
-            if (in.kind == BATCH_SWEPT) {
+            if (!CLS || in.kind == BATCH_SWEPT) {
                 const int odd = (int)(p & 1);
                 kl = odd ? (k + K - 1) % K : k;
                 kr = odd ? k : (k + 1) % K;
@@ -812,14 +815,13 @@ __global__ void __launch_bounds__(MODE == EULER ? 256 : 1024) swept_batch_kernel
         }
         __syncthreads();
         if (abort_s) break;
-        if constexpr (MODE == EULER) {
-            if (in.kind == BATCH_SWEPT) batch_item<R, EULER, false>(in, k, p, smem_raw);
-            else classic_item<R, EULER>(in, k, p, smem_raw);
-        } else if (in.kind == BATCH_SWEPT) {
-            if (in.eq == HEAT) batch_item<R, HEAT, REG>(in, k, p, smem_raw);
+        if (!CLS || in.kind == BATCH_SWEPT) {
+            if constexpr (MODE == EULER) batch_item<R, EULER, false>(in, k, p, smem_raw);
+            else if (in.eq == HEAT) batch_item<R, HEAT, REG>(in, k, p, smem_raw);
             else batch_item<R, KS, REG>(in, k, p, smem_raw);
-        } else {
-            if (in.eq == HEAT) classic_item<R, HEAT>(in, k, p, smem_raw);
+        } else if constexpr (CLS) {
+            if constexpr (MODE == EULER) classic_item<R, EULER>(in, k, p, smem_raw);
+            else if (in.eq == HEAT) classic_item<R, HEAT>(in, k, p, smem_raw);
             else classic_item<R, KS>(in, k, p, smem_raw);
         }
         __threadfence();
@@ -886,22 +888,22 @@ cudaError_t register_launch_eq(R* A, R* B, const PhaseGeom& g, const Coefs<R>& c
     return cudaGetLastError();
 }
 
-template <typename R, int MODE, bool REG>
+template <typename R, int MODE, bool REG, bool CLS>
 cudaError_t batch_launch_mode(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
                               cudaStream_t s)
 {
-    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, w.smem_bytes);
+    cudaError_t e = set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG, CLS>, w.smem_bytes);
     if (e != cudaSuccess) return e;
-    swept_batch_kernel<R, MODE, REG><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
+    swept_batch_kernel<R, MODE, REG, CLS><<<blocks, threads, w.smem_bytes, s>>>(insts, w);
     return cudaGetLastError();
 }
 
-template <typename R, int MODE, bool REG>
+template <typename R, int MODE, bool REG, bool CLS>
 int batch_bps_mode(size_t smem, int threads)
 {
-    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG>, smem) != cudaSuccess) return 0;
+    if (set_smem<R, MODE>((const void*)swept_batch_kernel<R, MODE, REG, CLS>, smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE, REG>, threads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, swept_batch_kernel<R, MODE, REG, CLS>, threads, smem) !=
         cudaSuccess)
         return 0;
     return nb;
@@ -952,20 +954,30 @@ cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const 
 }
 
 template <typename R>
-cudaError_t launch_swept_batch(int mode, bool reg, const BatchInst<R>* insts, const BatchWork& w, int threads,
-                               int blocks, cudaStream_t s)
+cudaError_t launch_swept_batch(int mode, bool reg, bool cls, const BatchInst<R>* insts, const BatchWork& w,
+                               int threads, int blocks, cudaStream_t s)
 {
-    if (mode == EULER) return batch_launch_mode<R, EULER, false>(insts, w, threads, blocks, s);
-    if (reg) return batch_launch_mode<R, HEAT, true>(insts, w, threads, blocks, s);
-    return batch_launch_mode<R, HEAT, false>(insts, w, threads, blocks, s);
+    if (mode == EULER)
+        return cls ? batch_launch_mode<R, EULER, false, true>(insts, w, threads, blocks, s)
+                   : batch_launch_mode<R, EULER, false, false>(insts, w, threads, blocks, s);
+    if (reg)
+        return cls ? batch_launch_mode<R, HEAT, true, true>(insts, w, threads, blocks, s)
+                   : batch_launch_mode<R, HEAT, true, false>(insts, w, threads, blocks, s);
+    return cls ? batch_launch_mode<R, HEAT, false, true>(insts, w, threads, blocks, s)
+               : batch_launch_mode<R, HEAT, false, false>(insts, w, threads, blocks, s);
 }
 
 template <typename R>
-int swept_batch_blocks_per_sm(int mode, bool reg, size_t smem_bytes, int threads)
+int swept_batch_blocks_per_sm(int mode, bool reg, bool cls, size_t smem_bytes, int threads)
 {
-    if (mode == EULER) return batch_bps_mode<R, EULER, false>(smem_bytes, threads);
-    if (reg) return batch_bps_mode<R, HEAT, true>(smem_bytes, threads);
-    return batch_bps_mode<R, HEAT, false>(smem_bytes, threads);
+    if (mode == EULER)
+        return cls ? batch_bps_mode<R, EULER, false, true>(smem_bytes, threads)
+                   : batch_bps_mode<R, EULER, false, false>(smem_bytes, threads);
+    if (reg)
+        return cls ? batch_bps_mode<R, HEAT, true, true>(smem_bytes, threads)
+                   : batch_bps_mode<R, HEAT, true, false>(smem_bytes, threads);
+    return cls ? batch_bps_mode<R, HEAT, false, true>(smem_bytes, threads)
+               : batch_bps_mode<R, HEAT, false, false>(smem_bytes, threads);
 }
 
 int swept_reg_slots(int eq, int n, int threads, int elem_bytes)
@@ -975,15 +987,15 @@ int swept_reg_slots(int eq, int n, int threads, int elem_bytes)
     return eq == HEAT ? reg_slots<double, HEAT>(n, threads) : reg_slots<double, KS>(n, threads);
 }
 
-template cudaError_t launch_swept_batch<double>(int, bool, const BatchInst<double>*, const BatchWork&, int,
-                                                int, cudaStream_t);
-template cudaError_t launch_swept_batch<float>(int, bool, const BatchInst<float>*, const BatchWork&, int,
+template cudaError_t launch_swept_batch<double>(int, bool, bool, const BatchInst<double>*, const BatchWork&,
+                                                int, int, cudaStream_t);
+template cudaError_t launch_swept_batch<float>(int, bool, bool, const BatchInst<float>*, const BatchWork&, int,
                                                int, cudaStream_t);
 template cudaError_t launch_swept_register<double>(int, double*, double*, const PhaseGeom&,
                                                    const Coefs<double>&, int, cudaStream_t);
 template cudaError_t launch_swept_register<float>(int, float*, float*, const PhaseGeom&,
                                                   const Coefs<float>&, int, cudaStream_t);
-template int swept_batch_blocks_per_sm<double>(int, bool, size_t, int);
-template int swept_batch_blocks_per_sm<float>(int, bool, size_t, int);
+template int swept_batch_blocks_per_sm<double>(int, bool, bool, size_t, int);
+template int swept_batch_blocks_per_sm<float>(int, bool, bool, size_t, int);
 
 }  // namespace swp
