@@ -89,7 +89,7 @@ def alu_roofline(updates: float, seconds: float, eq: str, dtype: str) -> dict:
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of the whole 10^4-step solve in
     # one dataflow launch: a one-pass capture of the benchmark's own timed launch
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "380626afd303d2d7", "bytes_per_launch": 11968256},
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "1ce8bb6dcae690b1", "bytes_per_launch": 11832320},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
@@ -105,7 +105,7 @@ def _code_only(text: str) -> str:
 
 def _kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("swept.cu", "scheme.cuh", "launch.h"):
+    for f in ("swept.cu", "geometry.cuh", "scheme.cuh", "launch.h"):
         with open(os.path.join(ROOT, "paper_1705_03162_gb300", "csrc", f), encoding="utf-8") as fh:
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -536,7 +536,8 @@ def other_configs() -> dict:
     device-timed, with the swept result checked bit for bit against the
     classic one.  Heat reports both swept forms, Shared (64-point nodes, CUDA
     graph) and the paper's Register variant (32-point warp nodes, graph), and
-    the faster as `swept`."""
+    the faster as `swept`; and the Register variant on one thread-block
+    cluster (the whole advance in one launch)."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     out = {}
@@ -551,9 +552,12 @@ def other_configs() -> dict:
                 results["swept_shared"] = p.read()
                 t_reg = _time_solve(p, u0d, steps, "swept", 32, "register")
                 results["swept_register"] = p.read()
+                t_cl = _time_solve(p, u0d, steps, "swept", 32, "cluster")
+                results["swept_cluster"] = p.read()
                 rec["swept_shared_n64_graph"] = N * steps / t_sh / 1e9
                 rec["swept_register_graph"] = N * steps / t_reg / 1e9
-                t_sw = min(t_sh, t_reg)
+                rec["swept_register_cluster"] = N * steps / t_cl / 1e9
+                t_sw = min(t_sh, t_reg, t_cl)
             else:
                 t_sw = _time_solve(p, u0d, steps, "swept", 512, "persistent")
                 results["swept"] = p.read()
@@ -834,6 +838,7 @@ def run_sweep(steps: int = 2000):
                 classic = N * steps / _time_solve(p, u0d, steps, "classic", launch="graph") / 1e9
                 reg = N * steps / _time_solve(p, u0d, steps, "swept", 0, "register", 64) / 1e9
                 auto = N * steps / _time_solve(p, u0d, steps, "swept", 0, "auto") / 1e9
+                cluster = N * steps / _time_solve(p, u0d, steps, "swept", 0, "cluster") / 1e9 if N <= 4096 else None
                 best, cfg = 0.0, None
                 for n in (64, 128, 256, 512, 1024):
                     if N % n or N // n < 2:
@@ -845,7 +850,8 @@ def run_sweep(steps: int = 2000):
                             best, cfg = r, {"points_per_block": n, "launch": launch}
             print(json.dumps({"sweep": eq, "n_points": N, "timesteps": steps, "dtype": "f64", "unit": UNIT,
                               "classic_graph": classic, "swept": best, "swept_config": cfg, "auto": auto,
-                              "register": reg, "swept_speedup": best / classic, "runs": runs}), flush=True)
+                              "register": reg, "cluster": cluster, "swept_speedup": best / classic,
+                              "runs": runs}), flush=True)
 
 
 def run_sod(exps, steps: int, widths=None, threads=None):

@@ -101,12 +101,23 @@ typedef enum {
                                    launches as a CUDA graph, captured on first use
                                    for (scheme, n_steps, width, threads) and
                                    replayed afterwards */
-    SWP_LAUNCH_REGISTER = 4     /* the paper's Register variant (Section 5.1):
+    SWP_LAUNCH_REGISTER = 4,    /* the paper's Register variant (Section 5.1):
                                    one warp per node of 32 points, levels in
                                    registers, neighbours by warp shuffle; one
                                    kernel per phase, replayed as a CUDA graph
                                    like SWP_LAUNCH_GRAPH; periodic heat and KS
                                    only (points_per_block 32 or 0) */
+    SWP_LAUNCH_CLUSTER = 5      /* the Register variant's nodes on one
+                                   thread-block cluster: the whole advance in
+                                   one launch, the level rows in the blocks'
+                                   shared memory (distributed shared memory),
+                                   a cluster barrier between phases; for small
+                                   periodic heat and KS problems: N a multiple
+                                   of 32 with N / 32 = blocks (<= 16) x warps
+                                   per block (<= 8), i.e. N <= 4096; threads =
+                                   32 x warps per block (0 = the most blocks).
+                                   SWP_EUNSUPPORTED when such a cluster cannot
+                                   run on the device */
 } swp_launch;
 
 typedef struct {

@@ -20,8 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libswept.so")
-SOURCES = ["api.cu", "classic.cu", "swept.cu", "server.cu"]
-HEADERS = ["scheme.cuh", "launch.h"]
+SOURCES = ["api.cu", "classic.cu", "swept.cu", "register.cu", "server.cu"]
+HEADERS = ["scheme.cuh", "launch.h", "geometry.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -484,7 +484,7 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         if (o.scheme == SWP_SWEPT && o.points_per_block == 0) o.points_per_block = n;
     }
     if (o.scheme == SWP_SWEPT && o.points_per_block == 0 && o.launch != SWP_LAUNCH_REGISTER &&
-        default_width(p) == 0) {
+        o.launch != SWP_LAUNCH_CLUSTER && default_width(p) == 0) {
         // N is too small for two nodes of 4 rad points: the classic scheme,
         // whose result is the same
         o.scheme = SWP_CLASSIC;
@@ -513,6 +513,53 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         // its phases are short (16 levels of KS, 32 of heat), so they replay
         // as a CUDA graph rather than pay a stream launch each
         return run_graph<R>(p, steps, kGraphRegister, 32, thr, &s);
+    }
+    if (o.launch == SWP_LAUNCH_CLUSTER) {
+        if (p->desc.eq == SWP_EULER || p->desc.bc != SWP_BC_PERIODIC)
+            return fail(SWP_EUNSUPPORTED, "the cluster variant runs periodic heat and KS");
+        if (o.points_per_block != 0 && o.points_per_block != 32)
+            return fail(SWP_EINVAL, "the cluster variant's node is one warp: points_per_block 32 (or 0)");
+        if (p->N % 32 || p->N < 64) return fail(SWP_EINVAL, "the cluster variant needs n_points a multiple of 32, >= 64");
+        const int K = (int)std::min<int64_t>(p->N / 32, 1 << 20);
+        // blocks: the most (at most 16) that split the nodes evenly with at
+        // most 8 warps each, or as many as `threads` asks
+        int ctas = 0, warps = 0;
+        if (o.threads != 0) {
+            warps = o.threads / 32;
+            if (o.threads % 32 || warps < 1 || warps > 8 || K % warps || K / warps > 16)
+                return fail(SWP_EINVAL, "cluster threads must be 32 w (w <= 8) with n_points / 32 = w x (blocks <= 16)");
+            ctas = K / warps;
+        } else {
+            for (int cc = 16; cc >= 1; --cc)
+                if (K % cc == 0 && K / cc <= 8) {
+                    ctas = cc;
+                    warps = K / cc;
+                    break;
+                }
+            if (ctas == 0)
+                return fail(SWP_EINVAL, "the cluster variant holds at most 16 blocks of 8 nodes (n_points %lld)",
+                            (long long)p->N);
+        }
+        const SweptPlan s = plan_swept(p, steps, 32);
+        if (s.T == 0) return SWP_OK;
+        ClusterGeom g;
+        g.N = p->N;
+        g.H = s.H;
+        g.K = K;
+        g.Q = s.Q;
+        g.r = s.r;
+        g.n_phases = s.n_phases;
+        g.portion = (int)(p->N / ctas);
+        g.warps = ctas * warps;
+        if (swept_cluster_fits<R>(p->desc.eq, g, ctas, 32 * warps) <= 0)
+            return fail(SWP_EUNSUPPORTED, "a cluster of %d blocks of %d threads does not fit this device", ctas,
+                        32 * warps);
+        cudaError_t e = launch_swept_cluster<R>(p->desc.eq, (R*)p->rows[p->cur], (R*)p->rows[1 - p->cur], g,
+                                                coefs_of<R>(p), ctas, 32 * warps, p->stream);
+        p->launches++;
+        if (e != cudaSuccess) return cuda_fail(e, "cluster swept launch");
+        if (s.top & 1) p->cur = 1 - p->cur;
+        return SWP_OK;
     }
     // AUTO: in FP64 the dataflow (persistent) launch from N = 2^17 up, where
     // it measured faster than per-phase launches; per-phase launches below,

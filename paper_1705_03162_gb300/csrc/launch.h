@@ -49,6 +49,24 @@ template <typename R>
 cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
                                   int threads, cudaStream_t s);
 
+// The Register variant's whole advance on one thread-block cluster of ctas
+// blocks (small periodic heat / KS problems): block r keeps points
+// [r portion, (r + 1) portion) of both level rows in shared memory, a warp is
+// a node of 32 points, phases are separated by cluster barriers.
+struct ClusterGeom {
+    int64_t N;
+    int H, K;             // levels per half-cycle (32-point nodes), nodes N / 32
+    int64_t Q, r, n_phases;
+    int portion;          // points per block, N / ctas
+    int warps;            // warps of the cluster
+};
+template <typename R>
+cudaError_t launch_swept_cluster(int eq, R* A, R* B, const ClusterGeom& g, const Coefs<R>& c, int ctas,
+                                 int threads, cudaStream_t s);
+// Clusters of this shape that fit on the device at once (0: it cannot run).
+template <typename R>
+int swept_cluster_fits(int eq, const ClusterGeom& g, int ctas, int threads);
+
 // ---------------------------------------------------------------------------
 // Batched advance: many independent problems of one precision in one
 // persistent launch (heat and KS together; Euler in its own launch).  Work is

@@ -43,46 +43,12 @@
 // paper's split node) and the first/last nodes of even phases (whose widest
 // level reaches the ends) evaluate points next to a wall through a
 // boundary-aware gather.
+#include "geometry.cuh"
 #include "launch.h"
 
 namespace swp {
 
 namespace {
-
-// Slot q of a node window stands for global point g0 + q (mod N).
-template <int EQ> struct Shape {
-    static constexpr int RAD = EQ == HEAT ? 1 : 2;
-    static constexpr int NV = EQ == EULER ? 3 : 1;
-};
-
-__host__ __device__ __forceinline__ int window_width(int n, int rad) { return n + 2 * rad; }
-
-// First point of node k of the K nodes of n points (plus the remainder d
-// spread over them) that partition [0, N).
-__host__ __device__ __forceinline__ int64_t node_start(int64_t k, int n, int K, int d)
-{
-    return k * n + (k * d) / K;
-}
-
-// Window of the tile of node k in a phase: global point of slot 0 and the
-// tile's width nk (slots [rad, rad + nk) are its points).  Odd phases: n
-// points centred on the node boundary b_k; even phases: the whole node.
-__device__ __forceinline__ void tile_window(int k, int odd, int n, int K, int d, int rad, int64_t& g0, int& nk)
-{
-    const int64_t b = node_start(k, n, K, d);
-    if (odd) {
-        g0 = b - n / 2 - rad;
-        nk = n;
-    } else {
-        g0 = b - rad;
-        nk = (int)(node_start(k + 1, n, K, d) - b);
-    }
-}
-
-__device__ __forceinline__ int64_t wrap(int64_t g, int64_t N)
-{
-    return g < 0 ? g + N : (g >= N ? g - N : g);
-}
 
 // Stencil value at slot q + d for the point at slot q, applying the boundary
 // condition when the stencil crosses a domain end: mirror about the end point
@@ -530,78 +496,6 @@ __device__ __forceinline__ uint64_t global_ns()
 constexpr uint32_t kMaxPolls = 1u << 26;
 
 // ---------------------------------------------------------------------------
-// Register variant (Section 5.1): a node is one warp of 32 points; lane l
-// holds window slot rad + l of both level rows in registers, and the odd row's
-// halo slots (the rad outermost on each side) are held by every lane.  Stencil
-// neighbours come from warp shuffles (all 32 lanes always take part, so lanes
-// outside the shrinking triangle still supply their values), and levels are
-// warp-synchronous: no shared memory and no block barrier.  Periodic problems.
-// ---------------------------------------------------------------------------
-constexpr int kRegNode = 32;
-
-template <typename R, int EQ>
-__global__ void __launch_bounds__(256) swept_register_kernel(R* A, R* B, PhaseGeom g, Coefs<R> c)
-{
-    constexpr int RAD = Shape<EQ>::RAD;
-    constexpr int n = kRegNode;
-    const int lane = threadIdx.x & 31;
-    const int k = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (k >= g.K) return;   // whole warps only: K nodes, one per warp
-    const int H = g.H;
-    const int64_t xc = g.odd ? (int64_t)k * n : (int64_t)k * n + n / 2;
-    const int64_t g0 = xc - n / 2 - RAD;   // global point of window slot 0
-    const int64_t gl = wrap(g0 + RAD + lane, g.N);
-    R a0 = A[gl];
-    R a1 = R(0), hl[RAD], hr[RAD];
-#pragma unroll
-    for (int i = 0; i < RAD; ++i) hl[i] = hr[i] = R(0);
-    if (g.j_lo <= H) {
-        a1 = B[gl];
-#pragma unroll
-        for (int i = 0; i < RAD; ++i) {
-            hl[i] = B[wrap(g0 + i, g.N)];
-            hr[i] = B[wrap(g0 + n + RAD + i, g.N)];
-        }
-    }
-    const int cs = n / 2 + RAD;
-    for (int j = g.j_lo; j <= g.j_hi; ++j) {
-        const int w = RAD * (j <= H ? j : 2 * H - j);
-        const bool odd_level = j & 1;
-        const R src = odd_level ? a0 : a1;
-        R v[2 * RAD + 1];
-#pragma unroll
-        for (int d = -RAD; d <= RAD; ++d) {
-            const R s = __shfl_sync(0xffffffffu, src, (lane + d) & 31);
-            const int t = lane + d;
-            // the even row never needs its halo: its stencils stay inside
-            R hv = s;
-#pragma unroll
-            for (int i = 0; i < RAD; ++i) {
-                if (t == i - RAD) hv = hl[i];
-                if (t == n + i) hv = hr[i];
-            }
-            v[d + RAD] = hv;
-        }
-        const int slot = RAD + lane;
-        if (slot >= cs - w && slot < cs + w) {
-            if constexpr (EQ == HEAT) {
-                const R o = heat_point(v[0], v[1], v[2], c.fo);
-                if (odd_level) a1 = o;
-                else a0 = o;
-            } else {
-                const R o = ks_point(v[0], v[1], v[2], v[3], v[4], a0,
-                                     odd_level ? c.a1[0] : c.a1[1], odd_level ? c.a4[0] : c.a4[1],
-                                     odd_level ? c.beta[0] : c.beta[1], odd_level ? c.gam[0] : c.gam[1]);
-                if (odd_level) a1 = o;
-                else a0 = o;
-            }
-        }
-    }
-    A[gl] = a0;
-    if (lane >= RAD && lane < n - RAD) B[gl] = a1;
-}
-
-// ---------------------------------------------------------------------------
 // Persistent dataflow form: one launch runs every phase of one or many
 // problems (a single problem's SWP_LAUNCH_PERSISTENT advance is a batch of
 // one).
@@ -878,16 +772,6 @@ cudaError_t phase_launch_eq(int bc, R* A, R* B, const PhaseGeom& g, const Coefs<
     return phase_launch_pr<R, EQ, 0>(bc, A, B, g, c, threads, s);
 }
 
-template <typename R, int EQ>
-cudaError_t register_launch_eq(R* A, R* B, const PhaseGeom& g, const Coefs<R>& c, int threads,
-                               cudaStream_t s)
-{
-    const int64_t warps_per_block = threads / 32;
-    const int64_t blocks = (g.K + warps_per_block - 1) / warps_per_block;
-    swept_register_kernel<R, EQ><<<(unsigned)blocks, threads, 0, s>>>(A, B, g, c);
-    return cudaGetLastError();
-}
-
 template <typename R, int MODE, bool REG, bool CLS>
 cudaError_t batch_launch_mode(const BatchInst<R>* insts, const BatchWork& w, int threads, int blocks,
                               cudaStream_t s)
@@ -946,14 +830,6 @@ template cudaError_t launch_swept_phase<double>(int, int, double*, double*, cons
 template cudaError_t launch_swept_phase<float>(int, int, float*, float*, const PhaseGeom&,
                                                const Coefs<float>&, int, cudaStream_t);
 template <typename R>
-cudaError_t launch_swept_register(int eq, R* A, R* B, const PhaseGeom& g, const Coefs<R>& c,
-                                  int threads, cudaStream_t s)
-{
-    if (eq == HEAT) return register_launch_eq<R, HEAT>(A, B, g, c, threads, s);
-    return register_launch_eq<R, KS>(A, B, g, c, threads, s);
-}
-
-template <typename R>
 cudaError_t launch_swept_batch(int mode, bool reg, bool cls, const BatchInst<R>* insts, const BatchWork& w,
                                int threads, int blocks, cudaStream_t s)
 {
@@ -991,10 +867,6 @@ template cudaError_t launch_swept_batch<double>(int, bool, bool, const BatchInst
                                                 int, int, cudaStream_t);
 template cudaError_t launch_swept_batch<float>(int, bool, bool, const BatchInst<float>*, const BatchWork&, int,
                                                int, cudaStream_t);
-template cudaError_t launch_swept_register<double>(int, double*, double*, const PhaseGeom&,
-                                                   const Coefs<double>&, int, cudaStream_t);
-template cudaError_t launch_swept_register<float>(int, float*, float*, const PhaseGeom&,
-                                                  const Coefs<float>&, int, cudaStream_t);
 template int swept_batch_blocks_per_sm<double>(int, bool, bool, size_t, int);
 template int swept_batch_blocks_per_sm<float>(int, bool, bool, size_t, int);
 

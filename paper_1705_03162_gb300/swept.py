@@ -24,14 +24,14 @@ HEAT, KS, EULER = 0, 1, 2
 PERIODIC, REFLECTIVE, DIRICHLET = 0, 1, 2
 F64, F32 = 0, 1
 CLASSIC, SWEPT, SCHEME_AUTO = 0, 1, 2
-LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH, LAUNCH_REGISTER = 0, 1, 2, 3, 4
+LAUNCH_AUTO, LAUNCH_PER_PHASE, LAUNCH_PERSISTENT, LAUNCH_GRAPH, LAUNCH_REGISTER, LAUNCH_CLUSTER = 0, 1, 2, 3, 4, 5
 
 _EQ = {"heat": HEAT, "ks": KS, "euler": EULER}
 _BC = {"periodic": PERIODIC, "reflective": REFLECTIVE, "dirichlet": DIRICHLET}
 _SCHEME = {"classic": CLASSIC, "swept": SWEPT, "auto": SCHEME_AUTO}
 _SCHEME_NAME = {CLASSIC: "classic", SWEPT: "swept"}
 _LAUNCH = {"auto": LAUNCH_AUTO, "per_phase": LAUNCH_PER_PHASE, "persistent": LAUNCH_PERSISTENT,
-           "graph": LAUNCH_GRAPH, "register": LAUNCH_REGISTER}
+           "graph": LAUNCH_GRAPH, "register": LAUNCH_REGISTER, "cluster": LAUNCH_CLUSTER}
 _DTYPE = {"f64": F64, "f32": F32}
 
 # every symbol include/swept.h declares

@@ -46,9 +46,10 @@ def _solo(spec, u0, steps, dtype):
 def test_served_results_equal_solo_and_oracle():
     reqs = _requests()
     budget = 3 * max(2 * u0.nbytes for _, u0, _, _ in reqs)   # a few requests at a time
-    # a small round target: each round pays for a few phases per request, so
-    # most requests span several rounds, with others in the same launches
-    with S.Server(hbm_budget_bytes=budget, max_active=4, round_target_ms=0.01) as srv:
+    # a tiny round target: nearly every request is longer than a round, so
+    # each runs a phase or a few per round and spans many rounds, with the
+    # others in the same launches
+    with S.Server(hbm_budget_bytes=budget, max_active=4, round_target_ms=0.0005) as srv:
         ids = [None] * len(reqs)
 
         def feed(lo, hi, delay):
