@@ -89,8 +89,14 @@ typedef struct {
 
 /* How swp_advance_ex runs the swept scheme. */
 typedef enum {
-    SWP_LAUNCH_AUTO = 0,        /* library choice: PERSISTENT for FP64 from
-                                   N = 2^17, PER_PHASE otherwise */
+    SWP_LAUNCH_AUTO = 0,        /* library choice, from measurement, with
+                                   the default width: for periodic heat and
+                                   KS with N a multiple of 32, CLUSTER up to
+                                   N = 2048 (FP64) or 4096 (FP32), then
+                                   REGISTER up to 2^15 for FP64 heat and up
+                                   to 2^16 in FP32; otherwise in FP64 GRAPH
+                                   below 2^17 and PERSISTENT from 2^17, in
+                                   FP32 PER_PHASE */
     SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
                                    nodes synchronise at kernel boundaries */
     SWP_LAUNCH_PERSISTENT = 2,  /* one dataflow kernel for the whole advance
@@ -115,7 +121,8 @@ typedef enum {
                                    periodic heat and KS problems: N a multiple
                                    of 32 with N / 32 = blocks (<= 16) x warps
                                    per block (<= 8), i.e. N <= 4096; threads =
-                                   32 x warps per block (0 = the most blocks).
+                                   32 x warps per block (0 = the most
+                                   blocks).
                                    SWP_EUNSUPPORTED when such a cluster cannot
                                    run on the device */
 } swp_launch;

@@ -474,6 +474,59 @@ swp_status run_graph(swp_problem* p, int64_t steps, int scheme, int n, int threa
     return SWP_OK;
 }
 
+// The Register variant's whole advance on one thread-block cluster
+// (SWP_LAUNCH_CLUSTER).
+template <typename R>
+swp_status run_swept_cluster(swp_problem* p, int64_t steps, const swp_advance_opts& o)
+{
+    if (p->desc.eq == SWP_EULER || p->desc.bc != SWP_BC_PERIODIC)
+        return fail(SWP_EUNSUPPORTED, "the cluster variant runs periodic heat and KS");
+    if (o.points_per_block != 0 && o.points_per_block != 32)
+        return fail(SWP_EINVAL, "the cluster variant's node is one warp: points_per_block 32 (or 0)");
+    if (p->N % 32 || p->N < 64) return fail(SWP_EINVAL, "the cluster variant needs n_points a multiple of 32, >= 64");
+    const int K = (int)std::min<int64_t>(p->N / 32, 1 << 20);
+    // one warp per node: the most blocks (at most 16) that split the
+    // nodes evenly with at most 8 warps each (measured: 16 blocks of 2
+    // warps ran N = 1024 faster than 8 of 4), or as many as `threads` asks
+    int ctas = 0, warps = 0;
+    if (o.threads != 0) {
+        warps = o.threads / 32;
+        if (o.threads % 32 || warps < 1 || warps > 8 || K % warps || K / warps > 16)
+            return fail(SWP_EINVAL, "cluster threads must be 32 w (w <= 8) with n_points / 32 = w x (blocks <= 16)");
+        ctas = K / warps;
+    } else {
+        for (int cc = 16; cc >= 1; --cc)
+            if (K % cc == 0 && K / cc <= 8) {
+                ctas = cc;
+                warps = K / cc;
+                break;
+            }
+        if (ctas == 0)
+            return fail(SWP_EINVAL, "the cluster variant holds at most 16 blocks of 8 nodes (n_points %lld)",
+                        (long long)p->N);
+    }
+    const SweptPlan s = plan_swept(p, steps, 32);
+    if (s.T == 0) return SWP_OK;
+    ClusterGeom g;
+    g.N = p->N;
+    g.H = s.H;
+    g.K = K;
+    g.Q = s.Q;
+    g.r = s.r;
+    g.n_phases = s.n_phases;
+    g.portion = (int)(p->N / ctas);
+    g.warps = ctas * warps;
+    if (swept_cluster_fits<R>(p->desc.eq, g, ctas, 32 * warps) <= 0)
+        return fail(SWP_EUNSUPPORTED, "a cluster of %d blocks of %d threads does not fit this device", ctas,
+                    32 * warps);
+    cudaError_t e = launch_swept_cluster<R>(p->desc.eq, (R*)p->rows[p->cur], (R*)p->rows[1 - p->cur], g,
+                                            coefs_of<R>(p), ctas, 32 * warps, p->stream);
+    p->launches++;
+    if (e != cudaSuccess) return cuda_fail(e, "cluster swept launch");
+    if (s.top & 1) p->cur = 1 - p->cur;
+    return SWP_OK;
+}
+
 template <typename R>
 swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& o_in)
 {
@@ -498,6 +551,25 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         }
         return run_classic<R>(p, steps, o.threads);
     }
+    // AUTO for small periodic heat and KS, where phases are short and launch
+    // gaps and global round trips count (measured fastest on GB300): the
+    // cluster form up to 2048 points in FP64 and 4096 in FP32 (heat FP32
+    // N = 1024: 11.9 G point-updates/s against 2.2 for per-phase launches),
+    // then the Register variant (graph) for heat up to 2^15 in FP64 and for
+    // heat and KS up to 2^16 in FP32; a cluster that cannot run falls through
+    if (o.launch == SWP_LAUNCH_AUTO && o.points_per_block == 0 && o.threads == 0 && p->desc.eq != SWP_EULER &&
+        p->desc.bc == SWP_BC_PERIODIC && p->N % 32 == 0 && p->N >= 64) {
+        const bool f32 = p->desc.dtype == SWP_F32;
+        if (p->N <= (f32 ? 4096 : 2048)) {
+            swp_advance_opts oc = o;
+            oc.launch = SWP_LAUNCH_CLUSTER;
+            swp_status st = run_swept_cluster<R>(p, steps, oc);
+            if (st != SWP_EUNSUPPORTED && st != SWP_EINVAL) return st;   // else no cluster shape fits N
+        }
+        if (f32 ? p->N <= ((int64_t)1 << 16) : (p->desc.eq == SWP_HEAT && p->N <= ((int64_t)1 << 15)))
+            o.launch = SWP_LAUNCH_REGISTER;
+    }
+    if (o.launch == SWP_LAUNCH_CLUSTER) return run_swept_cluster<R>(p, steps, o);
     if (o.launch == SWP_LAUNCH_REGISTER) {
         if (p->desc.eq == SWP_EULER || p->desc.bc != SWP_BC_PERIODIC)
             return fail(SWP_EUNSUPPORTED, "the register variant runs periodic heat and KS");
@@ -514,59 +586,16 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         // as a CUDA graph rather than pay a stream launch each
         return run_graph<R>(p, steps, kGraphRegister, 32, thr, &s);
     }
-    if (o.launch == SWP_LAUNCH_CLUSTER) {
-        if (p->desc.eq == SWP_EULER || p->desc.bc != SWP_BC_PERIODIC)
-            return fail(SWP_EUNSUPPORTED, "the cluster variant runs periodic heat and KS");
-        if (o.points_per_block != 0 && o.points_per_block != 32)
-            return fail(SWP_EINVAL, "the cluster variant's node is one warp: points_per_block 32 (or 0)");
-        if (p->N % 32 || p->N < 64) return fail(SWP_EINVAL, "the cluster variant needs n_points a multiple of 32, >= 64");
-        const int K = (int)std::min<int64_t>(p->N / 32, 1 << 20);
-        // blocks: the most (at most 16) that split the nodes evenly with at
-        // most 8 warps each, or as many as `threads` asks
-        int ctas = 0, warps = 0;
-        if (o.threads != 0) {
-            warps = o.threads / 32;
-            if (o.threads % 32 || warps < 1 || warps > 8 || K % warps || K / warps > 16)
-                return fail(SWP_EINVAL, "cluster threads must be 32 w (w <= 8) with n_points / 32 = w x (blocks <= 16)");
-            ctas = K / warps;
-        } else {
-            for (int cc = 16; cc >= 1; --cc)
-                if (K % cc == 0 && K / cc <= 8) {
-                    ctas = cc;
-                    warps = K / cc;
-                    break;
-                }
-            if (ctas == 0)
-                return fail(SWP_EINVAL, "the cluster variant holds at most 16 blocks of 8 nodes (n_points %lld)",
-                            (long long)p->N);
-        }
-        const SweptPlan s = plan_swept(p, steps, 32);
-        if (s.T == 0) return SWP_OK;
-        ClusterGeom g;
-        g.N = p->N;
-        g.H = s.H;
-        g.K = K;
-        g.Q = s.Q;
-        g.r = s.r;
-        g.n_phases = s.n_phases;
-        g.portion = (int)(p->N / ctas);
-        g.warps = ctas * warps;
-        if (swept_cluster_fits<R>(p->desc.eq, g, ctas, 32 * warps) <= 0)
-            return fail(SWP_EUNSUPPORTED, "a cluster of %d blocks of %d threads does not fit this device", ctas,
-                        32 * warps);
-        cudaError_t e = launch_swept_cluster<R>(p->desc.eq, (R*)p->rows[p->cur], (R*)p->rows[1 - p->cur], g,
-                                                coefs_of<R>(p), ctas, 32 * warps, p->stream);
-        p->launches++;
-        if (e != cudaSuccess) return cuda_fail(e, "cluster swept launch");
-        if (s.top & 1) p->cur = 1 - p->cur;
-        return SWP_OK;
-    }
     // AUTO: in FP64 the dataflow (persistent) launch from N = 2^17 up, where
-    // it measured faster than per-phase launches; per-phase launches below,
-    // and in FP32, where the per-phase kernels' register-blocked levels win
+    // it measured faster than per-phase launches, and below that the
+    // per-phase launches replayed as a CUDA graph (captured on the first
+    // advance of a step count; measured 5-10 % faster than stream launches);
+    // in FP32 per-phase launches, where the per-phase kernels'
+    // register-blocked levels win
     const int launch = o.launch != SWP_LAUNCH_AUTO ? o.launch
-                       : (p->N >= ((int64_t)1 << 17) && p->desc.dtype == SWP_F64) ? SWP_LAUNCH_PERSISTENT
-                                                                                  : SWP_LAUNCH_PER_PHASE;
+                       : p->desc.dtype != SWP_F64          ? SWP_LAUNCH_PER_PHASE
+                       : p->N >= ((int64_t)1 << 17)        ? SWP_LAUNCH_PERSISTENT
+                                                           : SWP_LAUNCH_GRAPH;
     int n = o.points_per_block;
     if (n == 0) {
         n = default_width(p, launch == SWP_LAUNCH_PERSISTENT);

@@ -126,39 +126,52 @@ __global__ void __launch_bounds__(256) swept_cluster_kernel(R* A, R* B, ClusterG
         rowA[i] = A[p0 + i];
         rowB[i] = B[p0 + i];
     }
-    cluster.sync();
     const int lane = threadIdx.x & 31;
-    const int warp = rank * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
+    // one node per warp (the host makes the cluster's warps equal the nodes)
+    const int k = rank * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5);
     const int H = g.H;
-    // the slot of global point x (any integer) in the owning block's row
-    auto at = [&](R* row, int64_t x) -> R* {
-        const int64_t gx = x < 0 ? x + g.N : (x >= g.N ? x - g.N : x);
-        return cluster.map_shared_rank(row, (unsigned)(gx / g.portion)) + (gx % g.portion);
+    // the slot of global point x (within one period of [0, N)) in the owning
+    // block's row; the tile of node k starts at k n (even phases) or
+    // k n - n / 2 (odd phases), so each lane's slots are found once here
+    const int N = (int)g.N;
+    auto at = [&](R* row, int x) -> R* {
+        const int gx = x < 0 ? x + N : (x >= N ? x - N : x);
+        return cluster.map_shared_rank(row, (unsigned)(gx / g.portion)) + gx % g.portion;
     };
+    R *pa[2], *pb[2], *phl[2][RAD], *phr[2][RAD];
+#pragma unroll
+    for (int odd = 0; odd < 2; ++odd) {
+        const int x0 = odd ? k * n - n / 2 : k * n;
+        pa[odd] = at(rowA, x0 + lane);
+        pb[odd] = at(rowB, x0 + lane);
+#pragma unroll
+        for (int i = 0; i < RAD; ++i) {
+            phl[odd][i] = at(rowB, x0 - RAD + i);
+            phr[odd][i] = at(rowB, x0 + n + i);
+        }
+    }
+    cluster.sync();
     for (int64_t ph = 0; ph < g.n_phases; ++ph) {
         const int odd = (int)(ph & 1);
         const int j_lo = ph == 0 ? H + 1 : 1;
         const int j_hi = ph < g.Q ? 2 * H - 1 : (ph == g.Q ? H + (int)g.r : (int)g.r);
-        for (int k = warp; k < g.K; k += g.warps) {
-            const int64_t x0 = odd ? (int64_t)k * n - n / 2 : (int64_t)k * n;   // first point of the tile
-            R* pa = at(rowA, x0 + lane);
-            R* pb = at(rowB, x0 + lane);
-            R a0 = *pa;
-            R a1 = R(0), hl[RAD], hr[RAD];
+        R* const a_ptr = odd ? pa[1] : pa[0];
+        R* const b_ptr = odd ? pb[1] : pb[0];
+        R a0 = *a_ptr;
+        R a1 = R(0), hl[RAD], hr[RAD];
 #pragma unroll
-            for (int i = 0; i < RAD; ++i) hl[i] = hr[i] = R(0);
-            if (j_lo <= H) {
-                a1 = *pb;
+        for (int i = 0; i < RAD; ++i) hl[i] = hr[i] = R(0);
+        if (j_lo <= H) {
+            a1 = *b_ptr;
 #pragma unroll
-                for (int i = 0; i < RAD; ++i) {
-                    hl[i] = *at(rowB, x0 - RAD + i);
-                    hr[i] = *at(rowB, x0 + n + i);
-                }
+            for (int i = 0; i < RAD; ++i) {
+                hl[i] = *(odd ? phl[1][i] : phl[0][i]);
+                hr[i] = *(odd ? phr[1][i] : phr[0][i]);
             }
-            warp_node_levels<R, EQ>(a0, a1, hl, hr, j_lo, j_hi, H, c);
-            *pa = a0;
-            if (lane >= RAD && lane < n - RAD) *pb = a1;
         }
+        warp_node_levels<R, EQ>(a0, a1, hl, hr, j_lo, j_hi, H, c);
+        *a_ptr = a0;
+        if (lane >= RAD && lane < n - RAD) *b_ptr = a1;
         cluster.sync();
     }
     for (int i = threadIdx.x; i < g.portion; i += blockDim.x) {
