@@ -530,7 +530,7 @@ def run_served(count: int = 1000, seed: int = 20170509, budget: int = 1 << 30) -
     return res
 
 
-def other_configs() -> dict:
+def other_configs(which=("heat", "sod")) -> dict:
     """The heat configuration (N = 1024, r = 0.25, 4096 steps) and the Sod
     tube at N = 2^20 (4096 steps, dt/dx = 0.2): swept against classic, FP64,
     device-timed, with the swept result checked bit for bit against the
@@ -543,6 +543,8 @@ def other_configs() -> dict:
     out = {}
     for name, eq, N, steps in (("heat N=1024 r=0.25 4096 steps", "heat", 1024, 4096),
                                ("Sod Euler N=2^20 4096 steps n=512 dataflow", "euler", 1 << 20, 4096)):
+        if ("heat" if eq == "heat" else "sod") not in which:
+            continue
         spec, u0 = _spec_ic(eq, N)
         u0d = torch.from_numpy(u0).cuda()
         rec, results = {}, {}
@@ -906,6 +908,8 @@ def main():
                          "--points-per-block, when given, replaces the autotuned widths, and --threads sets "
                          "the batch's block size")
     ap.add_argument("--served", type=int, metavar="COUNT", help="print the served line for COUNT requests instead")
+    ap.add_argument("--other", choices=["heat", "sod"], nargs="+",
+                    help="print the heat-configuration and / or Sod line instead")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sweep, bandwidth, other-configuration, batched, served and FP32-error lines")
     args = ap.parse_args()
@@ -922,7 +926,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, wl)
         return
-    if args.batched is not None or args.sod is not None or args.sweep or args.bandwidth or args.served:
+    if args.batched is not None or args.sod is not None or args.sweep or args.bandwidth or args.served or args.other:
         from paper_1705_03162_gb300 import swept as S
         S.load_library()
     if args.batched is not None:
@@ -936,6 +940,8 @@ def main():
                 [args.threads] if args.threads else None)
     elif args.served:
         print(json.dumps({"served": run_served(args.served)}))
+    elif args.other:
+        print(json.dumps({"other_configs": other_configs(tuple(args.other))}))
     elif args.sweep or args.bandwidth:
         if args.sweep:
             run_sweep()
