@@ -6,7 +6,9 @@
 // loading) in shared memory.  Both evaluate the shared point update of
 // scheme.cuh.
 // Euler evaluates each interface flux once per tile (P per cell, G per
-// interface) instead of twice per cell.
+// interface) instead of twice per cell, and reuses each cell's velocity,
+// specific energy and sqrt(rho) on the interface sides the limiter leaves
+// first order.
 #include "launch.h"
 
 namespace swp {
@@ -54,8 +56,9 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
         R* P = sm + NV * SW;        // pressure of every staged cell
         R* G = P + SW;              // G[v][l]: interface between tile cells l-1 and l
         const int GW = TILE + 1;
+        R* Cc = G + 3 * GW;         // cached (u, e, sqrt(rho)) of staged cell s at Cc[k SW + s]
         for (int s = threadIdx.x; s < SW; s += T) {
-            P[s] = euler_pressure(sm[s], sm[SW + s], sm[2 * SW + s], c.gm1);
+            P[s] = euler_cell(sm[s], sm[SW + s], sm[2 * SW + s], c.gm1, Cc[s], Cc[SW + s], Cc[2 * SW + s]);
         }
         __syncthreads();
         for (int l = threadIdx.x; l < GW; l += T) {
@@ -63,8 +66,10 @@ __global__ void __launch_bounds__(256) classic_kernel(const R* __restrict__ src,
             const int sb = RAD + l;
             R qa[3] = {sm[sb - 1], sm[SW + sb - 1], sm[2 * SW + sb - 1]};
             R qb[3] = {sm[sb], sm[SW + sb], sm[2 * SW + sb]};
+            const R ca[3] = {Cc[sb - 1], Cc[SW + sb - 1], Cc[2 * SW + sb - 1]};
+            const R cb[3] = {Cc[sb], Cc[SW + sb], Cc[2 * SW + sb]};
             R g3[3];
-            euler_interface(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], c.gm1, c.ggm1, g3);
+            euler_interface_cached(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], ca, cb, c.gm1, c.ggm1, g3);
             G[l] = g3[0];
             G[GW + l] = g3[1];
             G[2 * GW + l] = g3[2];
@@ -211,7 +216,7 @@ cudaError_t classic_launch_eq(int bc, const R* src, const R* base, R* out, int64
     const int tile = threads * kClassicPointsPerThread;
     const int sw = tile + 2 * RAD;
     size_t smem = sizeof(R) * (size_t)NV * sw;
-    if (EQ == EULER) smem += sizeof(R) * ((size_t)sw + 3 * (size_t)(tile + 1));
+    if (EQ == EULER) smem += sizeof(R) * ((size_t)sw + 3 * (size_t)(tile + 1) + 3 * (size_t)sw);
     const int64_t blocks = (N + tile - 1) / tile;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(classic_kernel<R, EQ>,

@@ -132,13 +132,15 @@ __device__ __forceinline__ R limited_ratio(R num, R den)
 // (pb - pa)/(pa - pam) and gives QL = Qa + min(ratio, 1)/2 (Qb - Qa) when it
 // lies in (0, inf); the inverse ratio at cell b, (pb - pa)/(pbp - pb), gives
 // QR = Qb + min(inverse, 1)/2 (Qa - Qb); otherwise first order.
+// lfirst / rfirst: the side was left first order (a copy of its cell).
 template <typename R>
 __device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], R pam, R pa,
-                                                  R pb, R pbp, R ql[3], R qr[3])
+                                                  R pb, R pbp, R ql[3], R qr[3], bool& lfirst, bool& rfirst)
 {
     using F = Fp<R>;
     R num = F::sub(pb, pa), den = F::sub(pa, pam);
-    if (same_sign(num, den)) {
+    lfirst = !same_sign(num, den);
+    if (!lfirst) {
         R h = F::mul(R(0.5), limited_ratio(num, den));
 #pragma unroll
         for (int c = 0; c < 3; ++c) ql[c] = F::fma(h, F::sub(qb[c], qa[c]), qa[c]);
@@ -147,7 +149,8 @@ __device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], 
         for (int c = 0; c < 3; ++c) ql[c] = qa[c];
     }
     R num2 = F::sub(pbp, pb);
-    if (same_sign(num2, num)) {
+    rfirst = !same_sign(num2, num);
+    if (!rfirst) {
         R h = F::mul(R(0.5), limited_ratio(num, num2));
 #pragma unroll
         for (int c = 0; c < 3; ++c) qr[c] = F::fma(h, F::sub(qa[c], qb[c]), qb[c]);
@@ -155,6 +158,14 @@ __device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], 
 #pragma unroll
         for (int c = 0; c < 3; ++c) qr[c] = qb[c];
     }
+}
+
+template <typename R>
+__device__ __forceinline__ void euler_reconstruct(const R qa[3], const R qb[3], R pam, R pa,
+                                                  R pb, R pbp, R ql[3], R qr[3])
+{
+    bool lfirst, rfirst;
+    euler_reconstruct(qa, qb, pam, pa, pb, pbp, ql, qr, lfirst, rfirst);
 }
 
 // G = 2 Flux from the limited states: F(QR) + F(QL) + r_sp (QL - QR), with
@@ -196,6 +207,73 @@ __device__ __forceinline__ void euler_interface(const R qa[3], const R qb[3], R 
     R ql[3], qr[3];
     euler_reconstruct(qa, qb, pam, pa, pb, pbp, ql, qr);
     euler_flux(ql, qr, gm1, ggm1, G);
+}
+
+// ---------------------------------------------------------------------------
+// The same interface value with per-cell values reused.  Where the limiter
+// leaves a side first order (uniform regions: the pressure difference is 0),
+// the side state is its cell's state, and the flux's pressure, velocity,
+// specific energy e = E/rho and sqrt(rho) of that side are the cell's own.
+// euler_cell forms them once per cell with exactly the operations euler_flux
+// applies to a side state, so reusing them gives the same bits; a limited
+// side is computed as in euler_flux.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R euler_cell(R r, R m, R E, R gm1, R& u, R& e, R& s)
+{
+    R ir;
+    const R p = euler_pressure(r, m, E, gm1, u, ir);
+    e = Fp<R>::mul(E, ir);
+    s = Fp<R>::sqrt(r);
+    return p;
+}
+
+// Pressure, velocity, e and sqrt(rho) of a limited side state q.
+template <typename R>
+__device__ __forceinline__ R euler_side(const R q[3], R gm1, R& u, R& e, R& s)
+{
+    return euler_cell(q[0], q[1], q[2], gm1, u, e, s);
+}
+
+// ca / cb: (u, e, sqrt(rho)) of cells a and b (as euler_cell forms them).
+template <typename R>
+__device__ __forceinline__ void euler_interface_cached(const R qa[3], const R qb[3], R pam, R pa, R pb,
+                                                       R pbp, const R ca[3], const R cb[3], R gm1, R ggm1,
+                                                       R G[3])
+{
+    using F = Fp<R>;
+    R ql[3], qr[3];
+    bool lfirst, rfirst;
+    euler_reconstruct(qa, qb, pam, pa, pb, pbp, ql, qr, lfirst, rfirst);
+    R pl, ul, el, sl, pr, ur, er, sr;
+    if (lfirst) {
+        pl = pa;
+        ul = ca[0];
+        el = ca[1];
+        sl = ca[2];
+    } else {
+        pl = euler_side(ql, gm1, ul, el, sl);
+    }
+    if (rfirst) {
+        pr = pb;
+        ur = cb[0];
+        er = cb[1];
+        sr = cb[2];
+    } else {
+        pr = euler_side(qr, gm1, ur, er, sr);
+    }
+    R fl1 = F::fma(ql[1], ul, pl);
+    R fl2 = F::mul(ul, F::add(ql[2], pl));
+    R fr1 = F::fma(qr[1], ur, pr);
+    R fr2 = F::mul(ur, F::add(qr[2], pr));
+    R iw = F::rcp(F::add(sl, sr));
+    R usp = F::mul(F::fma(sl, ul, F::mul(sr, ur)), iw);
+    R esp = F::mul(F::fma(sl, el, F::mul(sr, er)), iw);
+    R c2 = F::mul(ggm1, F::fma(F::mul(R(-0.5), usp), usp, esp));
+    R rsp = F::add(F::sqrt(c2), F::abs(usp));
+    G[0] = F::fma(rsp, F::sub(ql[0], qr[0]), F::add(qr[1], ql[1]));
+    G[1] = F::fma(rsp, F::sub(ql[1], qr[1]), F::add(fr1, fl1));
+    G[2] = F::fma(rsp, F::sub(ql[2], qr[2]), F::add(fr2, fl2));
 }
 
 // Finite-volume RK2 stage: out = base - (h/dx)(Flux_{i+1/2} - Flux_{i-1/2})

@@ -173,7 +173,8 @@ __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R*
 
 // Advance levels j_lo..j_hi of one tile of nk points in shared memory.
 //   row0 / row1 : [NV][W] even / odd level rows, W = nk + 2 rad
-//   P, G        : Euler scratch, W pressures, [3][W + 1] + 3 interface values, 8 ghost values
+//   P, G        : Euler scratch, W pressures, [3][W + 1] + 3 interface values, 14 ghost values,
+//                 [3][W] cached cell values (euler_cell)
 //   wall        : the node may evaluate points next to a non-periodic end
 template <typename R, int EQ>
 __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk, int H, int j_lo,
@@ -218,12 +219,15 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
             }
         } else {
             const R kh = c.kh[stage];
-            // pressures of cells [lo-2, hi+2), interfaces [lo, hi], then cells
+            // pressures (and the cell values euler_cell caches) of cells
+            // [lo-2, hi+2), interfaces [lo, hi], then cells
             const int GW = W + 1;
             R* Gx = G + 3 * GW;   // wall nodes: the interface between cell N-1 and the right ghost
             // ghost states, variable v of the left / right end at Gh[2v] /
-            // Gh[2v + 1], and their pressures at Gh[6] / Gh[7]
+            // Gh[2v + 1], their pressures at Gh[6] / Gh[7] and their cached
+            // (u, e, sqrt(rho)) at Gh[8 + 2k] / Gh[9 + 2k]
             R* Gh = Gx + 3;
+            R* Cc = Gh + 14;      // cached (u, e, sqrt(rho)) of slot s at Cc[k W + s]
             // Slots wrap modulo N; next to a Dirichlet end s0 is the slot of
             // cell 0 (W when the window does not wrap), so slots below s0 hold
             // cells ..., N-2, N-1.  Periodic ends: no slot is special.
@@ -237,11 +241,12 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
                 Gh[threadIdx.x] = gs[0];
                 Gh[2 + threadIdx.x] = gs[1];
                 Gh[4 + threadIdx.x] = gs[2];
-                Gh[6 + threadIdx.x] = euler_pressure(gs[0], gs[1], gs[2], c.gm1);
+                Gh[6 + threadIdx.x] = euler_cell(gs[0], gs[1], gs[2], c.gm1, Gh[8 + threadIdx.x],
+                                                 Gh[10 + threadIdx.x], Gh[12 + threadIdx.x]);
             }
             for (int t = threadIdx.x; t < cnt + 4; t += T) {
                 const int s = lo - 2 + t;
-                P[s] = euler_pressure(src[s], src[W + s], src[2 * W + s], c.gm1);
+                P[s] = euler_cell(src[s], src[W + s], src[2 * W + s], c.gm1, Cc[s], Cc[W + s], Cc[2 * W + s]);
             }
             __syncthreads();
             for (int t = threadIdx.x; t <= cnt; t += T) {
@@ -254,22 +259,26 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
                     // ..., N-2, N-1 (slots < s0); a stencil cell on the other
                     // side of s0 is the ghost state of that end
                     const bool left_end = rep == 0 && sb >= s0;
-                    R q[2][3], p[4];
+                    R q[2][3], p[4], cc[2][3];
 #pragma unroll
                     for (int d = 0; d < 4; ++d) {
                         const int s = sb + d - 2;
                         const bool lg = left_end && s < s0, rg = !left_end && s >= s0;
                         const bool gh = lg || rg;
                         const R* cell = gh ? Gh + (rg ? 1 : 0) : src + s;
+                        const R* cache = gh ? Gh + 8 + (rg ? 1 : 0) : Cc + s;
                         const int vs = gh ? 2 : W;
                         p[d] = gh ? Gh[6 + (rg ? 1 : 0)] : P[s];
                         if (d == 1 || d == 2) {
 #pragma unroll
-                            for (int v = 0; v < 3; ++v) q[d - 1][v] = cell[v * vs];
+                            for (int v = 0; v < 3; ++v) {
+                                q[d - 1][v] = cell[v * vs];
+                                cc[d - 1][v] = cache[v * vs];
+                            }
                         }
                     }
                     R g3[3];
-                    euler_interface(q[0], q[1], p[0], p[1], p[2], p[3], c.gm1, c.ggm1, g3);
+                    euler_interface_cached(q[0], q[1], p[0], p[1], p[2], p[3], cc[0], cc[1], c.gm1, c.ggm1, g3);
                     R* o = rep ? Gx : G + sb;
                     const int os = rep ? 1 : GW;
                     o[0] = g3[0];
@@ -403,7 +412,7 @@ __host__ __device__ __forceinline__ size_t smem_elems(int n)
     constexpr int RAD = Shape<EQ>::RAD, NV = Shape<EQ>::NV;
     const size_t W = (size_t)window_width(n, RAD);
     size_t e = 2 * NV * W;
-    if (EQ == EULER) e += W + 3 * (W + 1) + 11;
+    if (EQ == EULER) e += W + 3 * (W + 1) + 17 + 3 * W;   // P, G, Gx, Gh, cached cell values
     else e += kExchangeElems<EQ>;   // warp-edge exchange of the register-blocked levels
     return e;
 }
@@ -621,14 +630,18 @@ __device__ __forceinline__ void classic_item(const BatchInst<R>& in, int k, int6
         R* P = sm + NV * W;   // pressure of every staged cell
         R* G = P + W;         // G[v][l]: interface between chunk cells l-1 and l
         const int GW = cnt + 1;
-        for (int s = threadIdx.x; s < W; s += T) P[s] = euler_pressure(sm[s], sm[W + s], sm[2 * W + s], in.c.gm1);
+        R* Cc = G + 3 * GW;   // cached (u, e, sqrt(rho)) of staged cell s at Cc[k W + s]
+        for (int s = threadIdx.x; s < W; s += T)
+            P[s] = euler_cell(sm[s], sm[W + s], sm[2 * W + s], in.c.gm1, Cc[s], Cc[W + s], Cc[2 * W + s]);
         __syncthreads();
         for (int l = threadIdx.x; l <= cnt; l += T) {
             const int sb = RAD + l;
             const R qa[3] = {sm[sb - 1], sm[W + sb - 1], sm[2 * W + sb - 1]};
             const R qb[3] = {sm[sb], sm[W + sb], sm[2 * W + sb]};
+            const R ca[3] = {Cc[sb - 1], Cc[W + sb - 1], Cc[2 * W + sb - 1]};
+            const R cb[3] = {Cc[sb], Cc[W + sb], Cc[2 * W + sb]};
             R g3[3];
-            euler_interface(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], in.c.gm1, in.c.ggm1, g3);
+            euler_interface_cached(qa, qb, P[sb - 2], P[sb - 1], P[sb], P[sb + 1], ca, cb, in.c.gm1, in.c.ggm1, g3);
             G[l] = g3[0];
             G[GW + l] = g3[1];
             G[2 * GW + l] = g3[2];
@@ -800,7 +813,7 @@ size_t batch_classic_smem_bytes(int eq, int m, int elem_bytes)
     const size_t rad = eq == HEAT ? 1 : 2, nv = eq == EULER ? 3 : 1;
     const size_t W = (size_t)m + 2 * rad;
     size_t e = nv * W;
-    if (eq == EULER) e += W + 3 * ((size_t)m + 1);
+    if (eq == EULER) e += W + 3 * ((size_t)m + 1) + 3 * W;   // P, G, cached cell values
     return (size_t)elem_bytes * e;
 }
 
