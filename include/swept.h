@@ -93,10 +93,11 @@ typedef enum {
                                    the default width: for periodic heat and
                                    KS with N a multiple of 32, CLUSTER up to
                                    N = 2048 (FP64) or 4096 (FP32), then
-                                   REGISTER up to 2^15 for FP64 heat and up
-                                   to 2^16 in FP32; otherwise in FP64 GRAPH
-                                   below 2^17 and PERSISTENT from 2^17, in
-                                   FP32 PER_PHASE */
+                                   REGISTER up to 2^15 for FP64 heat, 2^18
+                                   for FP32 heat, 2^17 for FP32 KS;
+                                   otherwise in FP64 GRAPH
+                                   below 2^17 and PERSISTENT from 2^17
+                                   (Euler: from 2^13), in FP32 PER_PHASE */
     SWP_LAUNCH_PER_PHASE = 1,   /* one kernel per triangle / diamond phase;
                                    nodes synchronise at kernel boundaries */
     SWP_LAUNCH_PERSISTENT = 2,  /* one dataflow kernel for the whole advance

@@ -196,9 +196,9 @@ swp_status check_width(const swp_problem* p, int n)
 }
 
 // Default node width, from the widths measured fastest on GB300 for single
-// problems: about N / 1024 points for heat and KS (N / 512 in the persistent
-// dataflow launch; at least 128, at most 1024) and N / 256 for Euler (64 to
-// 512).  The nearest width down to half the target that divides N and
+// problems: about N / 512 in the persistent dataflow launch, and otherwise
+// N / 1024 points for heat and KS in FP64, N / 128 in FP32 (at least 128, at
+// most 1024) and N / 256 for Euler (64 to 512).  The nearest width down to half the target that divides N and
 // is a multiple of 4 rad; else the target itself (rounded down to a multiple
 // of 4 rad), whose remainder widens some nodes; 0 when N is too small for
 // any (fewer than two nodes of 4 rad points).
@@ -208,7 +208,10 @@ int default_width(const swp_problem* p, bool dataflow = false)
     const bool euler = p->desc.eq == SWP_EULER;
     const int lo = euler ? 64 : 128;
     const int cap = euler ? 512 : 1024;
-    int64_t target = p->N / (euler ? 256 : (dataflow ? 512 : 1024));
+    // FP32 per-phase nodes: about N / 128 (2^17 heat: 1024-point nodes 287
+    // against 252 G point-updates/s for 128)
+    const bool f32 = p->desc.dtype == SWP_F32;
+    int64_t target = p->N / (dataflow ? 512 : (euler ? 256 : (f32 ? 128 : 1024)));
     if (target < lo) target = lo;
     if (target > cap) target = cap;
     if (target > p->N / 2) target = p->N / 2;
@@ -238,12 +241,12 @@ bool tuned_of(const swp_desc& d, Tuned* t)
 }
 
 // Swept node width for a problem: the tuned one if measured, else the
-// default rule.
-int width_for(const swp_problem* p)
+// default rule (for the dataflow launch, or for per-phase launches).
+int width_for(const swp_problem* p, bool dataflow = false)
 {
     Tuned t;
     if (tuned_of(p->desc, &t) && t.n_swept > 0 && check_width(p, t.n_swept) == SWP_OK) return t.n_swept;
-    return default_width(p);
+    return default_width(p, dataflow);
 }
 
 // Classic chunk width of a batched classic advance (points per item).
@@ -555,8 +558,9 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     // gaps and global round trips count (measured fastest on GB300): the
     // cluster form up to 2048 points in FP64 and 4096 in FP32 (heat FP32
     // N = 1024: 11.9 G point-updates/s against 2.2 for per-phase launches),
-    // then the Register variant (graph) for heat up to 2^15 in FP64 and for
-    // heat and KS up to 2^16 in FP32; a cluster that cannot run falls through
+    // then the Register variant (graph) for heat up to 2^15 in FP64, and in
+    // FP32 for heat up to 2^18 (2^18: 566 against 528) and KS up to 2^17; a
+    // cluster that cannot run falls through
     if (o.launch == SWP_LAUNCH_AUTO && o.points_per_block == 0 && o.threads == 0 && p->desc.eq != SWP_EULER &&
         p->desc.bc == SWP_BC_PERIODIC && p->N % 32 == 0 && p->N >= 64) {
         const bool f32 = p->desc.dtype == SWP_F32;
@@ -566,8 +570,9 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
             swp_status st = run_swept_cluster<R>(p, steps, oc);
             if (st != SWP_EUNSUPPORTED && st != SWP_EINVAL) return st;   // else no cluster shape fits N
         }
-        if (f32 ? p->N <= ((int64_t)1 << 16) : (p->desc.eq == SWP_HEAT && p->N <= ((int64_t)1 << 15)))
-            o.launch = SWP_LAUNCH_REGISTER;
+        const int64_t reg_max = f32 ? ((int64_t)1 << (p->desc.eq == SWP_HEAT ? 18 : 17))
+                                    : (p->desc.eq == SWP_HEAT ? ((int64_t)1 << 15) : 0);
+        if (p->N <= reg_max) o.launch = SWP_LAUNCH_REGISTER;
     }
     if (o.launch == SWP_LAUNCH_CLUSTER) return run_swept_cluster<R>(p, steps, o);
     if (o.launch == SWP_LAUNCH_REGISTER) {
@@ -586,16 +591,18 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
         // as a CUDA graph rather than pay a stream launch each
         return run_graph<R>(p, steps, kGraphRegister, 32, thr, &s);
     }
-    // AUTO: in FP64 the dataflow (persistent) launch from N = 2^17 up, where
-    // it measured faster than per-phase launches, and below that the
-    // per-phase launches replayed as a CUDA graph (captured on the first
-    // advance of a step count; measured 5-10 % faster than stream launches);
-    // in FP32 per-phase launches, where the per-phase kernels'
-    // register-blocked levels win
+    // AUTO: in FP64 the dataflow (persistent) launch from N = 2^17 up (Euler
+    // from 2^13: Sod 2^17, 256-cell nodes, 3.21 against 2.81 G
+    // point-updates/s for the best per-phase form), where it measured faster
+    // than per-phase launches, and below that the per-phase launches replayed
+    // as a CUDA graph (captured on the first advance of a step count;
+    // measured 5-10 % faster than stream launches); in FP32 per-phase
+    // launches, where the per-phase kernels' register-blocked levels win
+    const bool euler = p->desc.eq == SWP_EULER;
     const int launch = o.launch != SWP_LAUNCH_AUTO ? o.launch
-                       : p->desc.dtype != SWP_F64          ? SWP_LAUNCH_PER_PHASE
-                       : p->N >= ((int64_t)1 << 17)        ? SWP_LAUNCH_PERSISTENT
-                                                           : SWP_LAUNCH_GRAPH;
+                       : p->desc.dtype != SWP_F64                      ? SWP_LAUNCH_PER_PHASE
+                       : p->N >= ((int64_t)1 << (euler ? 13 : 17))     ? SWP_LAUNCH_PERSISTENT
+                                                                       : SWP_LAUNCH_GRAPH;
     int n = o.points_per_block;
     if (n == 0) {
         n = default_width(p, launch == SWP_LAUNCH_PERSISTENT);
@@ -607,8 +614,8 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     if (threads == 0) {
         if (p->desc.dtype == SWP_F32)   // about 8 points per thread (register-blocked levels)
             threads = std::max(64, std::min(256, n / 8)) / 32 * 32;
-        else if (launch == SWP_LAUNCH_PERSISTENT)   // measured: 256 from 256-point nodes up
-            threads = n >= 256 ? 256 : (n >= 128 ? 128 : 64);
+        else if (launch == SWP_LAUNCH_PERSISTENT)   // measured: 256 from 256-point nodes up (Euler: always)
+            threads = (n >= 256 || p->desc.eq == SWP_EULER) ? 256 : (n >= 128 ? 128 : 64);
         else
             threads = n >= 512 ? 256 : (n >= 128 ? 128 : 64);
     }
@@ -1320,7 +1327,7 @@ swp_status tune_swept(const swp_desc* desc, const void* u0_host, int32_t count, 
 
 namespace swp {
 
-int swept_width(const swp_problem* p) { return width_for(p); }
+int swept_width(const swp_problem* p) { return width_for(p, true); }
 
 int classic_chunk(const swp_problem* p) { return default_chunk(p); }
 

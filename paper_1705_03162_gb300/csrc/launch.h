@@ -140,7 +140,7 @@ struct PhaseRange {
     int64_t p_lo, p_hi;
     int kind;   // BatchKind
 };
-int swept_width(const swp_problem* p);    // the tuned or default node width (0: none)
+int swept_width(const swp_problem* p);    // the tuned or default dataflow node width (0: none)
 int classic_chunk(const swp_problem* p);  // the default classic chunk width
 int64_t phase_count(const swp_problem* p, int64_t steps, int kind, int n);
 swp_status batch_advance_phases(swp_batch* b, const PhaseRange* ranges, int count, int threads);
