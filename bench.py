@@ -89,7 +89,7 @@ def alu_roofline(updates: float, seconds: float, eq: str, dtype: str) -> dict:
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of the whole 10^4-step solve in
     # one dataflow launch: a one-pass capture of the benchmark's own timed launch
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "1ce8bb6dcae690b1", "bytes_per_launch": 11832320},
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "b68223c633515964", "bytes_per_launch": 11983872},
 }
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
