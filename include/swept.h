@@ -93,8 +93,9 @@ typedef enum {
                                    the default width: for periodic heat and
                                    KS with N a multiple of 32, CLUSTER up to
                                    N = 2048 (FP64) or 4096 (FP32), then
-                                   REGISTER up to 2^15 for FP64 heat, 2^18
-                                   for FP32 heat, 2^17 for FP32 KS;
+                                   REGISTER up to 2^15 for FP64 heat, 2^14
+                                   for FP64 KS, 2^18 for FP32 heat, 2^17 for
+                                   FP32 KS;
                                    otherwise in FP64 GRAPH
                                    below 2^17 and PERSISTENT from 2^17
                                    (Euler: from 2^13), in FP32 PER_PHASE */

@@ -558,9 +558,9 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
     // gaps and global round trips count (measured fastest on GB300): the
     // cluster form up to 2048 points in FP64 and 4096 in FP32 (heat FP32
     // N = 1024: 11.9 G point-updates/s against 2.2 for per-phase launches),
-    // then the Register variant (graph) for heat up to 2^15 in FP64, and in
-    // FP32 for heat up to 2^18 (2^18: 566 against 528) and KS up to 2^17; a
-    // cluster that cannot run falls through
+    // then the Register variant (graph) up to 2^15 (heat) and 2^14 (KS) in
+    // FP64, and in FP32 for heat up to 2^18 (2^18: 566 against 528) and KS up
+    // to 2^17; a cluster that cannot run falls through
     if (o.launch == SWP_LAUNCH_AUTO && o.points_per_block == 0 && o.threads == 0 && p->desc.eq != SWP_EULER &&
         p->desc.bc == SWP_BC_PERIODIC && p->N % 32 == 0 && p->N >= 64) {
         const bool f32 = p->desc.dtype == SWP_F32;
@@ -571,7 +571,7 @@ swp_status advance_typed(swp_problem* p, int64_t steps, const swp_advance_opts& 
             if (st != SWP_EUNSUPPORTED && st != SWP_EINVAL) return st;   // else no cluster shape fits N
         }
         const int64_t reg_max = f32 ? ((int64_t)1 << (p->desc.eq == SWP_HEAT ? 18 : 17))
-                                    : (p->desc.eq == SWP_HEAT ? ((int64_t)1 << 15) : 0);
+                                    : ((int64_t)1 << (p->desc.eq == SWP_HEAT ? 15 : 14));
         if (p->N <= reg_max) o.launch = SWP_LAUNCH_REGISTER;
     }
     if (o.launch == SWP_LAUNCH_CLUSTER) return run_swept_cluster<R>(p, steps, o);

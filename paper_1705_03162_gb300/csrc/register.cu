@@ -37,19 +37,23 @@ __device__ __forceinline__ void warp_node_levels(R& a0, R& a1, const R (&hl)[Sha
         const int w = RAD * (j <= H ? j : 2 * H - j);
         const bool odd_level = j & 1;
         const R src = odd_level ? a0 : a1;
+        // stencil values v[RAD + d] = slot lane + d: the lane's own value,
+        // neighbours by shuffle up / down, and beyond the warp's ends the odd
+        // row's halo (slot -RAD + i is hl[i], slot n + i is hr[i]; the even
+        // row never needs its halo: its stencils stay inside)
         R v[2 * RAD + 1];
+        v[RAD] = src;
 #pragma unroll
-        for (int d = -RAD; d <= RAD; ++d) {
-            const R s = __shfl_sync(0xffffffffu, src, (lane + d) & 31);
-            const int t = lane + d;
-            // the even row never needs its halo: its stencils stay inside
-            R hv = s;
+        for (int d = 1; d <= RAD; ++d) {
+            R lo_v = __shfl_up_sync(0xffffffffu, src, d);
+            R hi_v = __shfl_down_sync(0xffffffffu, src, d);
 #pragma unroll
-            for (int i = 0; i < RAD; ++i) {
-                if (t == i - RAD) hv = hl[i];
-                if (t == n + i) hv = hr[i];
+            for (int l = 0; l < d; ++l) {
+                if (lane == l) lo_v = hl[RAD - d + l];
+                if (lane == n - d + l) hi_v = hr[l];
             }
-            v[d + RAD] = hv;
+            v[RAD - d] = lo_v;
+            v[RAD + d] = hi_v;
         }
         const int slot = RAD + lane;
         if (slot >= cs - w && slot < cs + w) {
