@@ -140,3 +140,31 @@ def test_served_any_n_matches_oracle():
         for rid, spec, u0, st in ids:
             got, _ = srv.wait(rid)
             assert np.array_equal(got, _oracle(spec, u0, st)), (spec.eq, spec.n_points)
+
+
+# sizes on each side of every boundary of the library's default launch choice
+# (cluster, Register graph, Shared graph, dataflow; FP32 per-phase)
+AUTO_CASES = [(eq, N, dt) for dt in ("f64", "f32") for eq in ("heat", "ks")
+              for N in (64, 1024, 2048, 4096, 8192, 1 << 14, (1 << 15) + 32, 1 << 17, (1 << 18) + 96)]
+
+
+@pytest.mark.parametrize("eq,N,dtype", AUTO_CASES)
+def test_default_launch_matches_oracle(eq, N, dtype):
+    spec = spec_for(eq, "periodic", N)
+    u0 = state_for(spec, np.float64 if dtype == "f64" else np.float32, seed=N)
+    steps = 61 if N <= (1 << 15) else 17
+    with S.Problem(spec, u0, dtype) as p:
+        p.advance(steps, "swept")          # SWP_LAUNCH_AUTO, default width
+        got = p.read()
+    assert np.array_equal(got, _oracle(spec, u0, steps))
+
+
+@pytest.mark.parametrize("N", [1 << 12, 1 << 13, (1 << 16) + 5, 1 << 18])
+def test_default_launch_euler_matches_oracle(N):
+    spec = spec_for("euler", "dirichlet", N)
+    u0 = state_for(spec, seed=N)
+    steps = 40
+    with S.Problem(spec, u0) as p:
+        p.advance(steps, "swept")
+        got = p.read()
+    assert np.array_equal(got, _oracle(spec, u0, steps))
