@@ -457,12 +457,17 @@ def fifo_latencies(arrivals, service):
     return lat
 
 
+def _digest(a: np.ndarray) -> str:
+    return hashlib.sha1(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
 def _serve(reqs, inputs, budget):
     """Submit reqs (arrival, eq, N, steps) at their arrival times to a server
-    with continuous batching; latencies, span and server statistics."""
+    with continuous batching; latencies, span, server statistics and a digest
+    of every result."""
     import threading
     from paper_1705_03162_gb300 import swept as S
-    with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=5.0) as srv:
+    with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=10.0) as srv:
         ids = [None] * len(reqs)
         t_start = time.perf_counter()
 
@@ -477,21 +482,27 @@ def _serve(reqs, inputs, budget):
         th = threading.Thread(target=feed)
         th.start()
         th.join()
-        lat = [srv.wait(i)[1] for i in ids]
+        lat, digests = [], []
+        for i in ids:
+            out, lt = srv.wait(i)
+            lat.append(lt)
+            digests.append(_digest(out))
         span = time.perf_counter() - t_start
         stats = srv.stats()
-    return lat, span, stats
+    return lat, span, stats, digests
 
 
 def run_served(count: int = 1000, seed: int = 20170509, budget: int = 1 << 30) -> dict:
     """Serving with continuous batching against one request at a time.
 
     One request set (served_requests, FP64) at three offered loads: an
-    overload trace (lam = 2000/s), whose completion rate is the server's
-    capacity C, then Poisson traces at 0.95 C and 0.7 C (the same arrival
-    pattern, rescaled).  The per-instance baseline is a FIFO queue over each
-    request's own solo solve (create, advance with the library default, read
-    back), timed once on the host clock and replayed against every trace."""
+    overload trace (lam = 2000/s), then Poisson traces at 0.95 and 0.7 of the
+    device's capacity for this mix solved one request at a time, C = count /
+    (the sum of the solo solve times), the same arrival pattern rescaled.  The
+    server's own capacity is its completion rate under overload.  The
+    per-instance baseline is a FIFO queue over each request's own solo solve
+    (create, advance with the library default, read back), timed once on the
+    host clock and replayed against every trace."""
     from paper_1705_03162_gb300 import swept as S
     base = served_requests(count, seed)
     inputs = [_spec_ic(eq, N) for _, eq, N, _ in base]
@@ -505,30 +516,33 @@ def run_served(count: int = 1000, seed: int = 20170509, budget: int = 1 << 30) -
     def trace(lam):
         return [(float(a / lam), eq, N, st) for a, (_, eq, N, st) in zip(unit_arrivals, base)]
 
-    # per-instance service times, one solve at a time
-    service = []
+    # per-instance service times, one solve at a time (and each result's
+    # digest: every served result must equal its solo solve bit for bit)
+    service, solo = [], []
     for (_, eq, N, st), (spec, u0) in zip(base, inputs):
         t0 = time.perf_counter()
         with S.Problem(spec, u0) as p:
             p.advance(st, "swept")
-            p.read()
+            out = p.read()
         service.append(time.perf_counter() - t0)
-    res["per_instance_capacity_req_per_s"] = count / sum(service)
-    lam, cap = 2000.0, None
-    for label, frac in (("overload", None), ("0.95 of capacity", 0.95), ("0.7 of capacity", 0.7)):
-        if frac is not None:
-            lam = frac * cap
+        solo.append(_digest(out))
+    cap = count / sum(service)
+    res["per_instance_capacity_req_per_s"] = cap
+    for label, lam in (("overload", 2000.0), ("0.95 of capacity", 0.95 * cap), ("0.7 of capacity", 0.7 * cap)):
         reqs = trace(lam)
-        lat, span, stats = _serve(reqs, inputs, budget)
-        if cap is None:
-            cap = count / span
-            res["capacity_req_per_s"] = cap
+        lat, span, stats, digests = _serve(reqs, inputs, budget)
+        differ = sum(1 for x, y in zip(digests, solo) if x != y)
+        if differ:
+            raise AssertionError(f"served ({label}): {differ} results differ from their solo solves")
+        if label == "overload":
+            res["capacity_req_per_s"] = count / span
         lat_b = fifo_latencies([r[0] for r in reqs], service)
         span_b = max(r[0] + l for r, l in zip(reqs, lat_b))
         res["loads"].append({
             "label": label, "lambda_per_s": lam, "offered_load": lam / cap,
             "served": dict(_percentiles(lat), throughput=upd / span / 1e9, unit=UNIT, rounds=stats["rounds"],
-                           kernel_launches=stats["kernel_launches"]),
+                           kernel_launches=stats["kernel_launches"],
+                           results_equal_solo_bitwise=f"{count - differ} of {count}"),
             "per_instance": dict(_percentiles(lat_b), throughput=upd / span_b / 1e9, unit=UNIT)})
     return res
 

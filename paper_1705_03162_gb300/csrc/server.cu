@@ -180,10 +180,10 @@ swp_status swp_server::round()
     // and retirement keeps the order).  A request whose remaining work fits in
     // one round's budget (a small one) runs all its remaining phases now, so
     // it never waits behind a long solve.  Longer ones run first come, first
-    // served: the oldest runs a round's budget of its phases, and younger ones
-    // join it only while the nodes of those already chosen leave blocks of the
-    // GPU idle (a narrow solve cannot fill the GPU by itself), each also with
-    // a round's budget.  A long solve therefore runs at nearly its solo speed
+    // served: the oldest runs a round's budget of its phases, and a younger
+    // one joins it only if its nodes fit in the blocks that those already
+    // chosen leave idle (a narrow solve cannot fill the GPU by itself), also
+    // with a round's budget.  A long solve therefore runs at nearly its solo speed
     // and waits only for long solves that arrived before it.
     // When every active request is long and none is pending, rounds are four
     // times longer: fewer rounds, less host work between them, and a request
@@ -209,7 +209,7 @@ swp_status swp_server::round()
             take[i] = left;
             continue;
         }
-        if (any_long && width >= width_cap) continue;
+        if (any_long && width + r.width > width_cap) continue;   // only into idle blocks
         take[i] = std::min<int64_t>(left, std::max<int64_t>(1, (int64_t)(long_budget / r.phase_cost)));
         width += r.width;
         any_long = true;
