@@ -91,6 +91,10 @@ NCU_TRAFFIC = {
     # one dataflow launch: a one-pass capture of the benchmark's own timed launch
     "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "b68223c633515964", "bytes_per_launch": 11983872},
 }
+# Issue-slot use of the batched FP32 launch from one ncu capture (512 instances
+# of the batched workload, 1024-point nodes): warp instructions issued over
+# 4 per SM per cycle, keyed like the traffic record.
+NCU_ISSUE_FP32_BATCH = {"src": "b68223c633515964", "issue_frac": 0.58, "issue_active": 0.605, "fma_pipe": 0.28}
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
 
@@ -410,7 +414,11 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
                                    "frac": flops / ms / 1e9 / peak, "pipe_ops_frac": ops / ms / 1e9 / (peak / 2),
                                    "flops": f"heat {op_count('heat'):g}, KS {op_count('ks'):g} per update "
                                             f"({eqs.count('heat')} heat, {eqs.count('ks')} KS)",
-                                   "peak_note": f"measured {'FP32' if dtype == 'f32' else 'FP64'} pipe"},
+                                   "peak_note": f"measured {'FP32' if dtype == 'f32' else 'FP64'} pipe",
+                                   "issue": (dict(NCU_ISSUE_FP32_BATCH, bound="issue",
+                                                  note="ncu capture of 512 instances of this workload")
+                                             if dtype == "f32" and NCU_ISSUE_FP32_BATCH["src"] == _kernel_src_hash()
+                                             else None)},
                       "tuned": {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}}
     return out
 

@@ -110,3 +110,10 @@ def test_bench_rejects_fewer_than_three_warmup_steps():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--warmup", "2"], capture_output=True,
                        text=True, timeout=120, cwd=ROOT)
     assert r.returncode == 2 and "--warmup must be >= 3" in r.stderr
+
+
+def test_issue_record_matches_the_kernel_code():
+    """The batched FP32 line's issue-slot figure comes from an ncu capture of
+    the current kernel code (re-capture after a kernel change)."""
+    assert bench.NCU_ISSUE_FP32_BATCH["src"] == bench._kernel_src_hash()
+    assert 0 < bench.NCU_ISSUE_FP32_BATCH["issue_frac"] <= 1
