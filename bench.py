@@ -89,12 +89,12 @@ def alu_roofline(updates: float, seconds: float, eq: str, dtype: str) -> dict:
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of the whole 10^4-step solve in
     # one dataflow launch: a one-pass capture of the benchmark's own timed launch
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "b68223c633515964", "bytes_per_launch": 11983872},
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "be34d6a20cd69d9d", "bytes_per_launch": 11685120},
 }
 # Issue-slot use of the batched FP32 launch from one ncu capture (512 instances
 # of the batched workload, 1024-point nodes): warp instructions issued over
 # 4 per SM per cycle, keyed like the traffic record.
-NCU_ISSUE_FP32_BATCH = {"src": "b68223c633515964", "issue_frac": 0.58, "issue_active": 0.605, "fma_pipe": 0.28}
+NCU_ISSUE_FP32_BATCH = {"src": "be34d6a20cd69d9d", "issue_frac": 0.63, "issue_active": 0.643, "fma_pipe": 0.334}
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
 

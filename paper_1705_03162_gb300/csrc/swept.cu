@@ -171,12 +171,76 @@ __device__ __forceinline__ void window_store(R* A, R* B, const R* row0, const R*
     }
 }
 
+// One heat / KS level of cnt points from slot lo (source row src, result row
+// dst; KS stage 1 takes its base values from dst, which is row 0 then), each
+// thread sweeping a contiguous run of the points with the stencil window in
+// registers: one shared-memory load per point instead of 2 rad + 1.  The runs
+// have odd length, so the threads of a warp address distinct banks while they
+// step together: the sweep goes 2 rad + 1 points at a time (the window turns
+// over once, so no register moves), then point by point; only a shorter last
+// run can fall out of step, in its last few points.  Each point takes the
+// same update from the same operands as in the strided loop.
+// tsh: log2 of the block size when that is a power of two, else -1.
+template <typename R, int EQ, int STAGE>
+__device__ __forceinline__ R run_point(const R (&v)[2 * Shape<EQ>::RAD + 1], const R* dst, int q,
+                                       const Coefs<R>& c)
+{
+    if constexpr (EQ == HEAT) {
+        return heat_point(v[0], v[1], v[2], c.fo);
+    } else {
+        const R base = STAGE == 0 ? v[2] : dst[q];
+        return ks_point(v[0], v[1], v[2], v[3], v[4], base, c.a1[STAGE], c.a4[STAGE], c.beta[STAGE],
+                        c.gam[STAGE]);
+    }
+}
+
+template <typename R, int EQ, int STAGE>
+__device__ __forceinline__ void level_runs(const R* src, R* dst, int lo, int cnt, int tsh, const Coefs<R>& c)
+{
+    constexpr int RAD = Shape<EQ>::RAD, U = 2 * RAD + 1;
+    const int T = blockDim.x, m = cnt + T - 1;
+    const int len = (tsh >= 0 ? m >> tsh : m / T) | 1;
+    int q = lo + (int)threadIdx.x * len;
+    const int end = min(q + len, lo + cnt);
+    if (q >= end) return;
+    R v[U];
+#pragma unroll
+    for (int k = 0; k < U - 1; ++k) v[k] = src[q - RAD + k];
+    for (; q + U <= end; q += U) {
+        // the block's loads first (the rows may alias as far as the compiler knows)
+        R nv[U], base[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            nv[u] = src[q + u + RAD];
+            base[u] = STAGE == 1 ? dst[q + u] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[U - 1] = nv[u];
+            if constexpr (EQ == HEAT)
+                dst[q + u] = heat_point(v[0], v[1], v[2], c.fo);
+            else
+                dst[q + u] = ks_point(v[0], v[1], v[2], v[3], v[4], STAGE == 0 ? v[2] : base[u], c.a1[STAGE],
+                                      c.a4[STAGE], c.beta[STAGE], c.gam[STAGE]);
+#pragma unroll
+            for (int k = 0; k < U - 1; ++k) v[k] = v[k + 1];
+        }
+    }
+    for (; q < end; ++q) {
+        v[U - 1] = src[q + RAD];
+        dst[q] = run_point<R, EQ, STAGE>(v, dst, q, c);
+#pragma unroll
+        for (int k = 0; k < U - 1; ++k) v[k] = v[k + 1];
+    }
+}
+
 // Advance levels j_lo..j_hi of one tile of nk points in shared memory.
 //   row0 / row1 : [NV][W] even / odd level rows, W = nk + 2 rad
 //   P, G        : Euler scratch, W pressures, [3][W + 1] + 3 interface values, 14 ghost values,
 //                 [3][W] cached cell values (euler_cell)
 //   wall        : the node may evaluate points next to a non-periodic end
-template <typename R, int EQ>
+//   RUNS        : FP32 heat / KS levels sweep contiguous runs (level_runs)
+template <typename R, int EQ, bool RUNS>
 __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk, int H, int j_lo,
                                             int j_hi, int64_t g0, int64_t N, bool wall, int bc,
                                             const Coefs<R>& c)
@@ -184,6 +248,7 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
     constexpr int RAD = Shape<EQ>::RAD;
     const int W = window_width(nk, RAD);
     const int T = blockDim.x;
+    const int tsh = (T & (T - 1)) == 0 ? __ffs(T) - 1 : -1;
     for (int j = j_lo; j <= j_hi; ++j) {
         // level j on slots [rad (1 + |j - H|), rad + nk - rad |j - H|): for a
         // tile of n = 2 rad H points, the 2 rad min(j, 2H - j) points around
@@ -194,6 +259,11 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
         const R* src = (j & 1) ? row0 : row1;
         const int stage = (EQ == HEAT) ? 0 : ((j & 1) ? 0 : 1);
         if constexpr (EQ == HEAT) {
+            if (RUNS && sizeof(R) == 4 && !wall) {
+                level_runs<R, EQ, 0>(src, dst, lo, cnt, tsh, c);
+                __syncthreads();
+                continue;
+            }
             for (int t = threadIdx.x; t < cnt; t += T) {
                 const int q = lo + t;
                 R tm, tp;
@@ -209,6 +279,12 @@ __device__ __forceinline__ void tile_levels(R* row0, R* row1, R* P, R* G, int nk
         } else if constexpr (EQ == KS) {
             // KS problems are periodic: the window is already wrapped.  (The
             // stage picks by value: c may be a copy in registers.)
+            if constexpr (RUNS && sizeof(R) == 4) {
+                if (stage) level_runs<R, EQ, 1>(src, dst, lo, cnt, tsh, c);
+                else level_runs<R, EQ, 0>(src, dst, lo, cnt, tsh, c);
+                __syncthreads();
+                continue;
+            }
             const R a1 = stage ? c.a1[1] : c.a1[0], a4 = stage ? c.a4[1] : c.a4[0];
             const R beta = stage ? c.beta[1] : c.beta[0], gam = stage ? c.gam[1] : c.gam[0];
             for (int t = threadIdx.x; t < cnt; t += T) {
@@ -451,7 +527,9 @@ __device__ __forceinline__ void run_levels(R* row0, R* row1, R* P, R* G, int n, 
             return;
         }
     }
-    tile_levels<R, EQ>(row0, row1, P, G, nk, H, j_lo, j_hi, g0, N, wall, bc, c);
+    // (tiles of the register-blocked kernels that fall back here, wider or
+    // next to a wall, keep the strided loop: fewer registers for the kernel)
+    tile_levels<R, EQ, PR == 0>(row0, row1, P, G, nk, H, j_lo, j_hi, g0, N, wall, bc, c);
 }
 
 template <typename R, int EQ, int PR>
