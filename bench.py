@@ -89,12 +89,14 @@ def alu_roofline(updates: float, seconds: float, eq: str, dtype: str) -> dict:
 NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum of the whole 10^4-step solve in
     # one dataflow launch: a one-pass capture of the benchmark's own timed launch
-    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "be34d6a20cd69d9d", "bytes_per_launch": 11685120},
+    "swept_batch_kernel<double,KS> n=1024 threads=256": {"src": "3b6f26f5347ef8b7", "bytes_per_launch": 11734272},
 }
-# Issue-slot use of the batched FP32 launch from one ncu capture (512 instances
-# of the batched workload, 1024-point nodes): warp instructions issued over
-# 4 per SM per cycle, keyed like the traffic record.
-NCU_ISSUE_FP32_BATCH = {"src": "be34d6a20cd69d9d", "issue_frac": 0.63, "issue_active": 0.643, "fma_pipe": 0.334}
+# Issue-slot use of the batched FP32 launch from one ncu capture (the 4096
+# instances of the batched workload, every node width 2048 fitted to N): warp
+# instructions issued over 4 per SM per cycle, keyed like the traffic record
+# and reported when the timed batch runs that width.
+NCU_ISSUE_FP32_BATCH = {"src": "3b6f26f5347ef8b7", "width": 2048, "issue_frac": 0.70, "issue_active": 0.703,
+                        "fma_pipe": 0.402}
 KERNEL_OF_LAUNCH = {"per_phase": "swept_phase_kernel", "graph": "swept_phase_kernel",
                     "persistent": "swept_batch_kernel", "auto": "swept_batch_kernel"}
 
@@ -313,13 +315,15 @@ def batched_cases(count: int = 4096, seed: int = 20170509):
 
 
 def fit_width(eq: str, N: int, n: int) -> int:
-    """A tuned power-of-two node width for a bucket, halved until it is valid
-    for N: it divides N, or leaves at least two nodes (the remainder widens
-    some of them)."""
+    """The node width for an instance of N points from its bucket's tuned
+    width n: N split into K = ceil(N / n) (at least 2) nodes of nearly equal
+    width, a multiple of 4 rad, the remainder widening some of them by less
+    than 4 rad.  No node is then wider than n + 4 rad, which bounds the shared
+    memory a batch's blocks are sized for (a width kept at n leaves nodes of
+    up to 1.5 n)."""
     step = 4 if eq == "heat" else 8
-    while n > step and not (N % n == 0 or N // n >= 2):
-        n //= 2
-    return n
+    K = max(2, -(-N // n))
+    return max(step, (N // K) // step * step)
 
 
 def bucket(N: int) -> int:
@@ -330,40 +334,71 @@ def bucket(N: int) -> int:
 def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), width: int = 0,
                 threads: int = 0) -> dict:
     """4096 independent heat + KS instances (batched_cases), one persistent
-    launch per precision replayed from a CUDA graph, scheme (swept or
-    classic) and node width autotuned per (equation, nearest power-of-two N)
-    bucket (or every instance swept at node width `width`); against advancing
-    a sample of the same instances one by one, whose results must equal the
-    batch's bit for bit."""
+    launch per precision replayed from a CUDA graph, against advancing a
+    sample of the same instances one by one, whose results must equal the
+    batch's bit for bit.  Node widths (or `width` for every instance): the
+    fastest, on one advance of the whole batch, of the library autotuner's
+    choice per (equation, nearest power-of-two N) bucket and of one width for
+    every instance (256, 512, 1024, 2048), each fitted to N (fit_width).  The
+    autotuner measures each bucket alone; in the mixed batch every block is
+    sized for the widest node, which can change the order."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     cases = batched_cases(count, seed)
     out = {"instances": count, "workload": "heat+KS, N log-uniform 2^10..2^16 (any integer), steps U(1e3,1e4)"}
+    steps = [c[2] for c in cases]
+    upd = float(sum(c[1] * c[2] for c in cases))
     for dtype in dtypes:
         npdt = np.float64 if dtype == "f64" else np.float32
-        t0 = time.perf_counter()
-        tuned = {}
-        for eq in ("heat", "ks"):
-            for e in range(10, 17):
-                spec, u0 = _spec_ic(eq, 2 ** e, npdt)
-                # enough copies (at least 2^21 points) to fill the GPU as the
-                # mixed batch does: a batch of a few small problems favours
-                # narrow nodes that lose in the full batch
-                tuned[(eq, e)] = ("swept", width) if width else S.autotune(
-                    spec, u0, count=max(256, (1 << 21) >> e), steps=128, dtype=dtype)
-        tune_s = time.perf_counter() - t0
         stream = torch.cuda.Stream()
-        probs, schemes, widths, inputs = [], [], [], []
-        for eq, N, steps in cases:
+        probs, inputs = [], []
+        for eq, N, _ in cases:
             spec, u0 = _spec_ic(eq, N, npdt)
             inputs.append((spec, u0))
             probs.append(S.Problem(spec, u0, dtype, stream=stream))
-            scheme, n = tuned[(eq, bucket(N))]
-            n = fit_width(eq, N, n) if scheme == "swept" else min(n, N)
-            schemes.append(scheme)
-            widths.append(n)
-        steps = [c[2] for c in cases]
-        upd = float(sum(c[1] * c[2] for c in cases))
+
+        def assign(choice):
+            """(schemes, widths) of a candidate: a bucket table or one width."""
+            sc, wd = [], []
+            for eq, N, _ in cases:
+                scheme, n = choice[(eq, bucket(N))] if isinstance(choice, dict) else ("swept", choice)
+                sc.append(scheme)
+                wd.append(fit_width(eq, N, n) if scheme == "swept" else min(n, N))
+            return sc, wd
+
+        def advance_ms(sc, wd, bt):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            bt.advance_ex(probs, steps, sc, wd, threads=threads, launch="persistent")
+            ev1.record(stream)
+            ev1.synchronize()
+            return ev0.elapsed_time(ev1)
+
+        t0 = time.perf_counter()
+        tuning = {}
+        if width:
+            chosen = width
+        else:
+            tuned = {}
+            for eq in ("heat", "ks"):
+                for e in range(10, 17):
+                    spec, u0 = _spec_ic(eq, 2 ** e, npdt)
+                    # enough copies (at least 2^21 points) to fill the GPU
+                    tuned[(eq, e)] = S.autotune(spec, u0, count=max(256, (1 << 21) >> e), steps=128, dtype=dtype)
+            tuning["per_bucket_autotune"] = {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}
+            cands = {"per-bucket autotune": tuned, "256": 256, "512": 512, "1024": 1024, "2048": 2048}
+            times = {}
+            with S.Batch(stream) as bt:
+                for name, choice in cands.items():
+                    times[name] = advance_ms(*assign(choice), bt)
+            for p, (_, u0) in zip(probs, inputs):   # back to the initial states
+                p.write(u0)
+            tuning["one_advance_ms"] = {k: round(v, 2) for k, v in times.items()}
+            best = min(times, key=times.get)
+            chosen = cands[best]
+            tuning["chosen"] = best
+        tune_s = time.perf_counter() - t0
+        schemes, widths = assign(chosen)
         with S.Batch(stream) as bt:
             # warm-up: two advances captured as CUDA graphs (an instance whose
             # advance ends in its other row alternates between two); the timed
@@ -380,7 +415,10 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
             ms = ev0.elapsed_time(ev1)
             launches = bt.kernel_launches() - l0
         # a sample advanced one problem at a time (the first advance timed),
-        # three advances like the batch's: the results must be the batch's bits
+        # the sample advanced one by one with the library defaults (scheme,
+        # launch and width chosen per problem), three advances like the
+        # batch's: every decomposition computes the same point updates, so the
+        # results must be the batch's bits
         sample = range(min(32, count))
         su = float(sum(cases[i][1] * cases[i][2] for i in sample))
         solo_s, mismatches = 0.0, 0
@@ -389,11 +427,11 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
             with S.Problem(spec, u0, dtype) as q:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
+                q.advance(steps[i], "auto")
                 q.synchronize()
                 solo_s += time.perf_counter() - t0
-                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
-                q.advance(steps[i], schemes[i], widths[i] if schemes[i] == "swept" else 0)
+                q.advance(steps[i], "auto")
+                q.advance(steps[i], "auto")
                 mismatches += int(not np.array_equal(q.read(), probs[i].read()))
         for p in probs:
             p.close()
@@ -416,10 +454,10 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
                                             f"({eqs.count('heat')} heat, {eqs.count('ks')} KS)",
                                    "peak_note": f"measured {'FP32' if dtype == 'f32' else 'FP64'} pipe",
                                    "issue": (dict(NCU_ISSUE_FP32_BATCH, bound="issue",
-                                                  note="ncu capture of 512 instances of this workload")
+                                                  note="ncu capture of this workload at that width")
                                              if dtype == "f32" and NCU_ISSUE_FP32_BATCH["src"] == _kernel_src_hash()
-                                             else None)},
-                      "tuned": {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}}
+                                             and chosen == NCU_ISSUE_FP32_BATCH["width"] else None)},
+                      "widths": tuning if tuning else f"every instance {width}, fitted to N"}
     return out
 
 

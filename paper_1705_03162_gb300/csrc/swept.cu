@@ -631,7 +631,9 @@ __device__ __forceinline__ void batch_item(const BatchInst<R>& in, int k, int64_
     __syncthreads();
     bool done = false;
     if constexpr (REG && EQ != EULER) {
-        done = !node_near_wall(in.bc, k, in.K) && nk == n;
+        // (the launch is register-blocked when some instance's nodes split
+        // evenly over the block; this instance's may not)
+        done = !node_near_wall(in.bc, k, in.K) && nk == n && n % (int)blockDim.x == 0;
         if (done) switch (n / (int)blockDim.x) {
         case 2: tile_levels_reg<R, EQ, 2>(row0, row1, P, n, H, j_lo, j_hi, c); break;
         case 4: tile_levels_reg<R, EQ, 4>(row0, row1, P, n, H, j_lo, j_hi, c); break;

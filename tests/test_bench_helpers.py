@@ -58,9 +58,12 @@ def test_batched_cases_and_widths():
     assert all(1024 <= N <= 65536 and 1000 <= st <= 10000 for _, N, st in cases)
     assert any(N % 128 for _, N, _ in cases)
     for eq, N, _ in cases:
-        n = bench.fit_width(eq, N, 1024)
-        assert N % n == 0 or N // n >= 2
-        assert n % (4 if eq == "heat" else 8) == 0
+        step = 4 if eq == "heat" else 8
+        for tuned in (256, 512, 1024):
+            n = bench.fit_width(eq, N, tuned)
+            K, d = N // n, N % n
+            assert K >= 2 and n % step == 0 and n <= tuned
+            assert n + -(-d // K) <= tuned + step   # the widest node
     assert bench.bucket(1024) == 10 and bench.bucket(65536) == 16 and bench.bucket(3000) == 12
 
 

@@ -244,3 +244,37 @@ def test_batch_graph_cache_after_problems_replaced():
                 assert np.array_equal(p.read(), ref)
                 p.close()
         assert b.kernel_launches() == 3
+
+
+def test_fp32_one_warp_batch_with_widths_off_the_block():
+    """An FP32 batch of one-warp blocks whose instances mix node widths that
+    split evenly over the warp (512: 16 register-blocked slots per lane, which
+    makes the launch register-blocked) with widths that do not (528, 520, 1000,
+    744: their levels stay in shared memory), with and without remainders:
+    every instance bit-identical to the oracle and to its solo advance."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    cases = [("heat", "periodic", 1024, 512), ("heat", "periodic", 1061, 528), ("ks", "periodic", 1061, 528),
+             ("heat", "reflective", 1583, 520), ("ks", "periodic", 2000, 1000), ("heat", "periodic", 1500, 744),
+             ("ks", "periodic", 2048, 512), ("heat", "periodic", 3169, 1056)]
+    probs, inputs, steps = [], [], []
+    for i, (eq, bc, N, n) in enumerate(cases):
+        spec = spec_for(eq, bc, N)
+        u0 = state_for(spec, np.float32, seed=N + n)
+        inputs.append((spec, u0))
+        probs.append(S.Problem(spec, u0, "f32", stream=stream))
+        steps.append(n + 61 + 17 * i)
+    widths = [c[3] for c in cases]
+    with S.Batch(stream) as b:
+        b.advance_ex(probs, steps, ["swept"] * len(cases), widths, threads=32, launch="graph")
+        b.synchronize()
+    got = [p.read() for p in probs]
+    for p in probs:
+        p.close()
+    for (eq, bc, N, n), (spec, u0), st, g in zip(cases, inputs, steps, got):
+        ref = np.ascontiguousarray(u0.copy())
+        O.classic(oprob(spec), ref, st)
+        assert np.array_equal(g, ref), (eq, bc, N, n, st)
+        with S.Problem(spec, u0, "f32") as q:
+            q.advance(st, "swept", n)
+            assert np.array_equal(q.read(), g), (eq, bc, N, n, st)

@@ -300,3 +300,25 @@ def test_fp32_register_blocked_levels(eq, bc, n, threads, launch):
         got = p.read()
     assert np.array_equal(got, ref), (eq, bc, n, threads, launch)
     assert np.array_equal(got, _gpu(spec, u0, steps, "f32", "classic"))
+
+
+@pytest.mark.parametrize("eq,bc", [("heat", "periodic"), ("heat", "reflective"), ("ks", "periodic")])
+@pytest.mark.parametrize("N,n,threads", [(10007, 1000, 96), (10007, 1000, 160), (8192, 2048, 64),
+                                         (6151, 2048, 32), (4099, 64, 224)])
+@pytest.mark.parametrize("launch", ["per_phase", "persistent"])
+def test_fp32_shared_memory_level_runs(eq, bc, N, n, threads, launch):
+    """FP32 heat / KS nodes beyond the register-blocked slot counts sweep
+    their levels in shared memory, each thread a contiguous run: block sizes
+    that are not powers of two (96, 160, 224: the run length by division),
+    runs of 32 and 64 slots, prime and odd N (wider nodes from the
+    remainder), and a block wider than the node.  Bit-identical to the oracle
+    and to classic."""
+    steps = 2 * (n // 2) + 37 if eq == "heat" else n + 37
+    spec = spec_for(eq, bc, N)
+    u0 = state_for(spec, np.float32, seed=N + n + threads)
+    ref = _oracle(spec, u0, steps)
+    with S.Problem(spec, u0, "f32") as p:
+        p.advance(steps, "swept", n, launch, threads)
+        got = p.read()
+    assert np.array_equal(got, ref), (eq, bc, N, n, threads, launch)
+    assert np.array_equal(got, _gpu(spec, u0, steps, "f32", "classic"))
