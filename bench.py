@@ -661,13 +661,14 @@ def fp32_error() -> dict:
 def sweep_line(steps: int = 500) -> dict:
     """Swept at the library default (SWP_LAUNCH_AUTO and the default width)
     against classic replayed as a CUDA graph, heat and KS FP64 at
-    N = 2^11..2^20 (the paper's size range, Section 6), with each one's
-    fraction of the FP64 pipe."""
+    N = 2^11..2^20 (the paper's size range, Section 6) and at 2^22 and 2^24,
+    where the two level rows no longer fit in L2, with each one's fraction of
+    the FP64 pipe."""
     import torch
     from paper_1705_03162_gb300 import swept as S
     pts = []
     for eq in ("heat", "ks"):
-        for e in range(11, 21):
+        for e in list(range(11, 21)) + [22, 24]:
             N = 1 << e
             spec, u0 = _spec_ic(eq, N)
             u0d = torch.from_numpy(u0).cuda()
