@@ -315,15 +315,11 @@ def batched_cases(count: int = 4096, seed: int = 20170509):
 
 
 def fit_width(eq: str, N: int, n: int) -> int:
-    """The node width for an instance of N points from its bucket's tuned
-    width n: N split into K = ceil(N / n) (at least 2) nodes of nearly equal
-    width, a multiple of 4 rad, the remainder widening some of them by less
-    than 4 rad.  No node is then wider than n + 4 rad, which bounds the shared
-    memory a batch's blocks are sized for (a width kept at n leaves nodes of
-    up to 1.5 n)."""
-    step = 4 if eq == "heat" else 8
-    K = max(2, -(-N // n))
-    return max(step, (N // K) // step * step)
+    """The node width for an instance of N points from a target width n: the
+    library's swp_fit_width (N split into max(2, ceil(N / n)) nearly equal
+    nodes, none wider than n + 4 rad)."""
+    from paper_1705_03162_gb300 import swept as S
+    return S.fit_width(eq, N, n)
 
 
 def bucket(N: int) -> int:
@@ -386,17 +382,19 @@ def run_batched(count: int = 4096, seed: int = 20170509, dtypes=("f64", "f32"), 
                     # enough copies (at least 2^21 points) to fill the GPU
                     tuned[(eq, e)] = S.autotune(spec, u0, count=max(256, (1 << 21) >> e), steps=128, dtype=dtype)
             tuning["per_bucket_autotune"] = {f"{k[0]}2^{k[1]}": f"{v[0]} {v[1]}" for k, v in tuned.items()}
-            cands = {"per-bucket autotune": tuned, "256": 256, "512": 512, "1024": 1024, "2048": 2048}
-            times = {}
+            uniform = (256, 512, 1024, 2048)
             with S.Batch(stream) as bt:
-                for name, choice in cands.items():
-                    times[name] = advance_ms(*assign(choice), bt)
+                # one width for every instance, fitted to each N, timed by the
+                # library on the batch itself (states put back after each)
+                _, best_u, ms_u = bt.tune_width(probs, steps, uniform, threads=threads)
+                # and the per-bucket autotuner's choice, timed the same way
+                ms_b = advance_ms(*assign(tuned), bt)
             for p, (_, u0) in zip(probs, inputs):   # back to the initial states
                 p.write(u0)
+            times = {"per-bucket autotune": ms_b, **{str(w): m for w, m in zip(uniform, ms_u)}}
             tuning["one_advance_ms"] = {k: round(v, 2) for k, v in times.items()}
-            best = min(times, key=times.get)
-            chosen = cands[best]
-            tuning["chosen"] = best
+            chosen = tuned if ms_b < ms_u[best_u] else uniform[best_u]
+            tuning["chosen"] = "per-bucket autotune" if isinstance(chosen, dict) else str(chosen)
         tune_s = time.perf_counter() - t0
         schemes, widths = assign(chosen)
         with S.Batch(stream) as bt:

@@ -283,6 +283,38 @@ swp_status swp_autotune(const swp_desc* desc, const void* u0_host, int32_t batch
 /* The tuned choice for desc's key: scheme and width (SWP_SWEPT, 0 if none). */
 swp_status swp_tuned(const swp_desc* desc, int32_t* scheme, int32_t* n);
 
+/* Node width for n_points points of equation eq from a target width:
+ * n_points split into K = max(2, ceil(n_points / target)) nearly equal nodes,
+ * the width a multiple of 4 rad (rad 1 for heat, 2 for KS and Euler), so that
+ * the remainder (Section 4.2's nodes all have n points; here any N is split)
+ * widens some nodes by at most 4 rad and no node is wider than
+ * target + 4 rad.  *n = 0 when n_points has no two nodes of 4 rad points.
+ * Host arithmetic only; SWP_EINVAL for an unknown eq, n_points or target <= 0,
+ * or n NULL. */
+swp_status swp_fit_width(int32_t eq, int64_t n_points, int32_t target, int32_t* n);
+
+/* Node widths for a mixed batch, measured on the batch itself.  For each of
+ * the n_candidates target widths, every problem's width is fitted to its N
+ * (swp_fit_width; 0, the default rule, where the fitted width is not valid
+ * for the problem) and problems[0..count) are advanced once by n_steps[i]
+ * (swept, one persistent launch per group, block size `threads` as for
+ * swp_batch_advance), timed with CUDA events on the batch's stream.  The
+ * fastest candidate's per-problem widths are written to widths_out[count],
+ * its index to *best (may be NULL), and each candidate's milliseconds to
+ * ms_out[n_candidates] (may be NULL).  The per-bucket autotuner
+ * (swp_autotune_width) times copies of one problem alone; in a mixed batch
+ * every block is sized for the widest node, which can change the order.
+ * The problems' states are saved to a device buffer this call allocates (the
+ * sum of their state sizes, not counted against swp_set_memory_budget) and
+ * put back after every trial, so the call leaves them as it found them.
+ * Synchronises the batch's stream.  Errors: SWP_EINVAL (NULL arguments,
+ * count or n_candidates <= 0, a candidate <= 0, a problem on another stream),
+ * SWP_ENOMEM (the save buffer), and those of swp_batch_advance_ex and
+ * swp_batch_synchronize, after the states are put back. */
+swp_status swp_batch_tune_width(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps, int32_t count,
+                                const int32_t* candidates, int32_t n_candidates, int32_t threads,
+                                int32_t* widths_out, float* ms_out, int32_t* best);
+
 /* ---- Serving with continuous batching ----
  * A server owns a scheduler thread that admits solve requests as they arrive
  * (in order, while its device-memory budget and slot count allow), keeps their

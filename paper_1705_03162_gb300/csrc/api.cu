@@ -1255,6 +1255,19 @@ swp_status batch_advance(swp_batch* b, swp_problem* const* problems, const int64
     return launch_groups(b, groups, threads, launch == SWP_LAUNCH_GRAPH);
 }
 
+// Node width for N points from a target width w: N split into
+// K = max(2, ceil(N / w)) nearly equal nodes, the width a multiple of 4 rad,
+// so that the remainder widens some nodes by at most 4 rad and no node is
+// wider than w + 4 rad (a batch sizes its blocks for its widest node); 0 when
+// N has no two nodes of 4 rad points.
+int64_t fitted_width(int rad, int64_t N, int64_t w)
+{
+    const int64_t step = 4 * rad;
+    if (w < step || N < 2 * step) return 0;
+    const int64_t K = std::max<int64_t>(2, (N + w - 1) / w);
+    return std::max<int64_t>(step, (N / K) / step * step);
+}
+
 // Time two advances (the second timed) of `steps` timesteps of `count`
 // copies of a problem in one batch with the given scheme and width; returns
 // point-updates per second, or < 0.
@@ -1537,6 +1550,92 @@ swp_status swp_tuned_width(const swp_desc* desc, int32_t* n)
     if (!n) return fail(SWP_EINVAL, "n is NULL");
     Tuned t;
     *n = tuned_of(*desc, &t) ? t.n_swept : 0;
+    return SWP_OK;
+}
+
+swp_status swp_fit_width(int32_t eq, int64_t n_points, int32_t target, int32_t* n)
+{
+    if (!n) return fail(SWP_EINVAL, "n is NULL");
+    *n = 0;
+    if (eq != SWP_HEAT && eq != SWP_KS && eq != SWP_EULER) return fail(SWP_EINVAL, "unknown equation %d", eq);
+    if (n_points <= 0 || target <= 0) return fail(SWP_EINVAL, "n_points and target must be > 0");
+    *n = (int32_t)fitted_width(eq == SWP_HEAT ? 1 : 2, n_points, target);
+    return SWP_OK;
+}
+
+swp_status swp_batch_tune_width(swp_batch* b, swp_problem* const* problems, const int64_t* n_steps, int32_t count,
+                                const int32_t* candidates, int32_t n_candidates, int32_t threads,
+                                int32_t* widths_out, float* ms_out, int32_t* best)
+{
+    if (!b || !problems || !n_steps || !candidates || !widths_out)
+        return fail(SWP_EINVAL, "batch, problems, n_steps, candidates or widths_out is NULL");
+    if (count <= 0 || n_candidates <= 0) return fail(SWP_EINVAL, "count and n_candidates must be > 0");
+    for (int32_t k = 0; k < n_candidates; ++k)
+        if (candidates[k] <= 0) return fail(SWP_EINVAL, "candidate width %d must be > 0", k);
+    for (int32_t i = 0; i < count; ++i) {
+        if (!problems[i]) return fail(SWP_EINVAL, "problem %d is NULL", i);
+        if (problems[i]->stream != b->stream) return fail(SWP_EINVAL, "problem %d uses another stream than the batch", i);
+    }
+    // the states, saved once and put back after every trial
+    std::vector<size_t> off(count), bytes(count);
+    std::vector<int> cur(count);
+    size_t total = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const swp_problem* p = problems[i];
+        bytes[i] = (size_t)p->nv * (size_t)p->N * (size_t)p->esize;
+        off[i] = total;
+        total += (bytes[i] + 255) / 256 * 256;
+        cur[i] = p->cur;
+    }
+    char* saved = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc((void**)&saved, total);
+    if (e != cudaSuccess) return fail(SWP_ENOMEM, "no device memory to save the states (%zu bytes)", total);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int32_t i = 0; i < count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(saved + off[i], problems[i]->rows[cur[i]], bytes[i], cudaMemcpyDeviceToDevice, b->stream);
+    swp_status st = e == cudaSuccess ? SWP_OK : cuda_fail(e, "save states");
+    std::vector<int32_t> w(count), best_w;
+    float best_ms = 0.0f;
+    int32_t best_k = -1;
+    for (int32_t k = 0; k < n_candidates && st == SWP_OK; ++k) {
+        for (int32_t i = 0; i < count; ++i) {
+            swp_problem* p = problems[i];
+            const int64_t n = fitted_width(p->rad, p->N, candidates[k]);
+            w[i] = n > 0 && n <= INT32_MAX && check_width(p, (int)n) == SWP_OK ? (int32_t)n : 0;
+        }
+        e = cudaEventRecord(e0, b->stream);
+        if (e != cudaSuccess) { st = cuda_fail(e, "tune event"); break; }
+        st = batch_advance(b, problems, n_steps, count, nullptr, SWP_SWEPT, w.data(), threads, SWP_LAUNCH_PERSISTENT);
+        if (st == SWP_OK && (e = cudaEventRecord(e1, b->stream)) != cudaSuccess) st = cuda_fail(e, "tune event");
+        if (st == SWP_OK) st = swp_batch_synchronize(b);
+        float ms = 0.0f;
+        if (st == SWP_OK && (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) st = cuda_fail(e, "tune timing");
+        // back to the saved states, whatever the trial did
+        for (int32_t i = 0; i < count; ++i) {
+            swp_problem* p = problems[i];
+            const cudaError_t er = cudaMemcpyAsync(p->rows[cur[i]], saved + off[i], bytes[i], cudaMemcpyDeviceToDevice,
+                                                   b->stream);
+            if (er != cudaSuccess && st == SWP_OK) st = cuda_fail(er, "restore states");
+            p->cur = cur[i];
+        }
+        if (st != SWP_OK) break;
+        if (ms_out) ms_out[k] = ms;
+        if (best_k < 0 || ms < best_ms) {
+            best_ms = ms;
+            best_k = k;
+            best_w = w;
+        }
+    }
+    e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess && st == SWP_OK) st = cuda_fail(e, "tune synchronize");
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(saved);
+    if (st != SWP_OK) return st;
+    std::copy(best_w.begin(), best_w.end(), widths_out);
+    if (best) *best = best_k;
     return SWP_OK;
 }
 

@@ -42,7 +42,7 @@ ABI_SYMBOLS = (
     "swp_status_str", "swp_last_error", "swp_swept_noalloc",
     "swp_batch_create", "swp_batch_advance", "swp_batch_synchronize", "swp_batch_destroy",
     "swp_batch_kernel_launches", "swp_autotune_width", "swp_tuned_width",
-    "swp_batch_advance_ex", "swp_autotune", "swp_tuned",
+    "swp_batch_advance_ex", "swp_autotune", "swp_tuned", "swp_fit_width", "swp_batch_tune_width",
     "swp_server_create", "swp_server_submit", "swp_server_poll", "swp_server_wait",
     "swp_server_stats", "swp_server_destroy",
 )
@@ -131,6 +131,10 @@ def load_library(path: str = LIB_PATH):
             "swp_autotune": ([ctypes.POINTER(Desc), vp, i32, i64, ctypes.POINTER(i32), ctypes.POINTER(i32)],
                              ctypes.c_int),
             "swp_tuned": ([ctypes.POINTER(Desc), ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_fit_width": ([i32, i64, i32, ctypes.POINTER(i32)], ctypes.c_int),
+            "swp_batch_tune_width": ([P, ctypes.POINTER(P), ctypes.POINTER(i64), i32, ctypes.POINTER(i32), i32, i32,
+                                      ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)],
+                                     ctypes.c_int),
             "swp_server_create": ([ctypes.POINTER(ServerConfig), vp, ctypes.POINTER(P)], ctypes.c_int),
             "swp_server_submit": ([P, ctypes.POINTER(Desc), vp, i64, ctypes.POINTER(i64)], ctypes.c_int),
             "swp_server_poll": ([P, i64, ctypes.POINTER(i32)], ctypes.c_int),
@@ -363,6 +367,22 @@ class Batch:
         _check(self._lib.swp_batch_advance_ex(self._h, hs, st, count, sc, nn, int(threads), _LAUNCH[launch]),
                "batch_advance_ex")
 
+    def tune_width(self, problems, steps, candidates=(256, 512, 1024, 2048), threads: int = 0):
+        """swp_batch_tune_width: each candidate target width fitted to every
+        problem's N and timed on one advance of the whole batch (states put
+        back after each); returns (widths of the fastest, its index, the
+        milliseconds of every candidate)."""
+        count, nc = len(problems), len(candidates)
+        hs = (ctypes.c_void_p * count)(*[p._h.value for p in problems])
+        st = _per_problem("steps", steps, count, ctypes.c_int64)
+        cand = (ctypes.c_int32 * nc)(*[int(c) for c in candidates])
+        out = (ctypes.c_int32 * count)()
+        ms = (ctypes.c_float * nc)()
+        best = ctypes.c_int32(-1)
+        _check(self._lib.swp_batch_tune_width(self._h, hs, st, count, cand, nc, int(threads), out, ms,
+                                              ctypes.byref(best)), "batch_tune_width")
+        return list(out), int(best.value), [float(x) for x in ms]
+
     def synchronize(self):
         _check(self._lib.swp_batch_synchronize(self._h), "batch_synchronize")
 
@@ -397,6 +417,14 @@ def autotune_width(spec: ProblemSpec, u0: np.ndarray, count: int = 16, steps: in
     _check(lib.swp_autotune_width(ctypes.byref(make_desc(spec, dtype)), u0.ctypes.data, int(count),
                                   int(steps), ctypes.byref(out)), "autotune_width")
     return out.value
+
+
+def fit_width(eq: str, n_points: int, target: int) -> int:
+    """swp_fit_width: the node width for n_points from a target width (N in
+    nearly equal nodes, none wider than target + 4 rad); 0 if none fits."""
+    out = ctypes.c_int32(0)
+    _check(load_library().swp_fit_width(_EQ[eq], int(n_points), int(target), ctypes.byref(out)), "fit_width")
+    return int(out.value)
 
 
 def tuned_width(spec: ProblemSpec, dtype: str = "f64") -> int:

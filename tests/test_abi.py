@@ -124,6 +124,32 @@ def test_tuning_and_batch_entry_points_validate_on_the_host(lib):
     assert lib.swp_batch_destroy(None) == S.OK
 
 
+def test_fit_width_splits_n_into_nearly_equal_nodes(lib):
+    """swp_fit_width (host arithmetic): at least two nodes, a multiple of
+    4 rad, no wider than the target, the remainder widening nodes by at most
+    4 rad; exact divisions keep the target; too-small N gives 0."""
+    def fit(eq, N, w):
+        out = ctypes.c_int32(-1)
+        assert lib.swp_fit_width(eq, N, w, ctypes.byref(out)) == S.OK
+        return out.value
+    assert fit(S.KS, 1 << 20, 1024) == 1024 and fit(S.HEAT, 4096, 1024) == 1024
+    assert fit(S.HEAT, 2049, 1024) == 680 and fit(S.KS, 3071, 1024) == 1016
+    assert fit(S.HEAT, 7, 1024) == 0 and fit(S.KS, 15, 1024) == 0 and fit(S.KS, 16, 1024) == 8
+    for eq, step in ((S.HEAT, 4), (S.KS, 8), (S.EULER, 8)):
+        for N in list(range(2 * step, 700)) + [1023, 1025, 40001, 65535, (1 << 20) + 3]:
+            for w in (step, 64, 100, 256, 1024, 2048):
+                n = fit(eq, N, w)
+                K, d = N // n, N % n
+                assert n % step == 0 and step <= n <= max(w, step) and K >= 2, (eq, N, w, n)
+                assert -(-d // K) <= step, (eq, N, w, n)
+    out = ctypes.c_int32(0)
+    assert lib.swp_fit_width(9, 1024, 256, ctypes.byref(out)) == S.EINVAL
+    assert lib.swp_fit_width(S.KS, 0, 256, ctypes.byref(out)) == S.EINVAL
+    assert lib.swp_fit_width(S.KS, 1024, 0, ctypes.byref(out)) == S.EINVAL
+    assert lib.swp_fit_width(S.KS, 1024, 256, None) == S.EINVAL
+    assert lib.swp_batch_tune_width(None, None, None, 0, None, 0, 0, None, None, None) == S.EINVAL
+
+
 def test_scheme_enum_matches_header():
     text = open(os.path.join(ROOT, "include", "swept.h")).read()
     assert "SWP_CLASSIC = 0" in text and "SWP_SWEPT = 1" in text and "SWP_SCHEME_AUTO = 2" in text

@@ -52,6 +52,8 @@ def test_fifo_latencies():
 
 
 def test_batched_cases_and_widths():
+    from paper_1705_03162_gb300 import build as B
+    B.build()
     cases = bench.batched_cases(512)
     assert cases == bench.batched_cases(512)
     assert [c[0] for c in cases[:4]] == ["heat", "ks", "heat", "ks"]

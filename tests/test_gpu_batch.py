@@ -278,3 +278,42 @@ def test_fp32_one_warp_batch_with_widths_off_the_block():
         with S.Problem(spec, u0, "f32") as q:
             q.advance(st, "swept", n)
             assert np.array_equal(q.read(), g), (eq, bc, N, n, st)
+
+
+def test_batch_tune_width_restores_states_and_returns_fitted_widths():
+    """swp_batch_tune_width times each candidate on the batch itself and puts
+    every state back (heat advances that end in the odd row included): the
+    states read after tuning equal those before, the widths returned are the
+    best candidate's widths fitted to each N, and an advance with them equals
+    the oracle bit for bit."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    cases = [("heat", "periodic", 1031, 501, "f64"), ("heat", "reflective", 2503, 377, "f64"),
+             ("ks", "periodic", 4099, 211, "f64"), ("heat", "periodic", 3001, 333, "f32"),
+             ("ks", "periodic", 2048, 150, "f32"), ("euler", "dirichlet", 1537, 97, "f64")]
+    probs, inputs = [], []
+    for eq, bc, N, steps, dtype in cases:
+        spec = spec_for(eq, bc, N)
+        u0 = state_for(spec, np.float64 if dtype == "f64" else np.float32, seed=N)
+        inputs.append((spec, u0))
+        probs.append(S.Problem(spec, u0, dtype, stream=stream))
+    steps = [c[3] for c in cases]
+    candidates = (64, 256, 1000)
+    with S.Batch(stream) as b:
+        # an odd first advance leaves some heat states in the other row
+        b.advance(probs, [1] * len(probs))
+        b.synchronize()
+        before = [p.read() for p in probs]
+        widths, best, ms = b.tune_width(probs, steps, candidates)
+        assert 0 <= best < len(candidates) and len(ms) == len(candidates) and min(ms) > 0
+        for p, x in zip(probs, before):
+            assert np.array_equal(p.read(), x)
+        for (eq, _, N, _, _), w in zip(cases, widths):
+            assert w == S.fit_width(eq, N, candidates[best]), (eq, N, w)
+        b.advance_ex(probs, steps, ["swept"] * len(probs), widths)
+        b.synchronize()
+    for (eq, bc, N, st, dtype), (spec, u0), p, x in zip(cases, inputs, probs, before):
+        ref = np.ascontiguousarray(u0.copy())
+        O.classic(oprob(spec), ref, 1 + st)
+        assert np.array_equal(p.read(), ref), (eq, bc, N, st, dtype)
+        p.close()
