@@ -320,8 +320,12 @@ swp_status swp_batch_tune_width(swp_batch* b, swp_problem* const* problems, cons
  * (in order, while its device-memory budget and slot count allow), keeps their
  * states resident on the device, and advances all admitted requests together
  * in rounds of batched launches; requests arriving meanwhile join the next
- * round.  Each result is bit-identical to solving the request alone.  The
- * paper has no serving layer. */
+ * round.  A round runs every request whose remaining work fits in
+ * round_target_ms to its end; longer ones run in order of their remaining
+ * work less the work done while they waited (shortest remaining first, aged,
+ * so that none is passed indefinitely), as many as fill the GPU.  Each result
+ * is bit-identical to solving the request alone.  The paper has no serving
+ * layer. */
 typedef struct swp_server swp_server;
 
 typedef struct {

@@ -11,8 +11,9 @@
 //    edges staying in its rows between rounds.  A round runs every request
 //    whose remaining work (estimated FP64 work per point-update of its
 //    equation) fits in a target round time to its end, and the long ones
-//    first come, first served: the oldest for a round's worth of phases,
-//    younger ones beside it while the GPU has idle blocks.  All of it goes
+//    shortest remaining work first, aged by their waiting time: the first
+//    for a round's worth of phases, others beside it while the GPU has idle
+//    blocks.  All of it goes
 //    into one batched launch per group (a round of one request below 2^17
 //    points, or in FP32, runs as that request's per-phase launches, as
 //    swp_advance would run it alone); requests that arrive meanwhile join
@@ -173,22 +174,28 @@ void swp_server::admit()
     }
 }
 
+// The work rate (operations per second) the round budget and the aging of
+// long requests are expressed in.
+constexpr double kOpsPerSecond = 4.0e11;
+
 swp_status swp_server::round()
 {
     // called without mu: the active list only changes on this thread.
-    // Requests are in arrival order (admission is first come, first served
-    // and retirement keeps the order).  A request whose remaining work fits in
-    // one round's budget (a small one) runs all its remaining phases now, so
-    // it never waits behind a long solve.  Longer ones run first come, first
-    // served: the oldest runs a round's budget of its phases, and a younger
-    // one joins it only if its nodes fit in the blocks that those already
-    // chosen leave idle (a narrow solve cannot fill the GPU by itself), also
-    // with a round's budget.  A long solve therefore runs at nearly its solo speed
-    // and waits only for long solves that arrived before it.
+    // A request whose remaining work fits in one round's budget (a small one)
+    // runs all its remaining phases now, so it never waits behind a long
+    // solve.  Longer ones go in order of their remaining work less the work
+    // the GPU does while they wait (remaining operations - age x the
+    // operation rate): the first runs a round's budget of its phases, and
+    // each next one joins only if its nodes fit in the blocks that those
+    // already chosen leave idle (a narrow solve cannot fill the GPU by
+    // itself), also with a round's budget.  Shorter solves thus pass longer
+    // ones, which keeps the many mid-size solves from queueing behind the few
+    // largest; a solve that has waited as long as its own remaining work
+    // ranks ahead of every newer one, which bounds how long it can be passed.
     // When every active request is long and none is pending, rounds are four
     // times longer: fewer rounds, less host work between them, and a request
     // arriving meanwhile waits at most one such round.
-    double budget_ops = cfg.round_target_ms * 1e-3 * 4.0e11;
+    double budget_ops = cfg.round_target_ms * 1e-3 * kOpsPerSecond;
     bool all_long = true;
     for (auto& rq : active)
         if ((double)(rq->n_phases - rq->phase_next) * rq->phase_cost <= budget_ops) all_long = false;
@@ -202,7 +209,17 @@ swp_status swp_server::round()
     std::vector<int64_t> take(active.size(), 0);
     int64_t width = 0;   // nodes (or chunks) per phase of the long solves chosen
     bool any_long = false;
+    const auto now = Clock::now();
+    std::vector<std::pair<double, size_t>> order(active.size());
     for (size_t i = 0; i < active.size(); ++i) {
+        const Request& r = *active[i];
+        const double age_s = std::chrono::duration<double>(now - r.t_submit).count();
+        order[i] = {(double)(r.n_phases - r.phase_next) * r.phase_cost - age_s * kOpsPerSecond, i};
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, size_t>& a, const std::pair<double, size_t>& b) { return a.first < b.first; });
+    for (const auto& o : order) {
+        const size_t i = o.second;
         Request& r = *active[i];
         const int64_t left = r.n_phases - r.phase_next;
         if ((double)left * r.phase_cost <= budget_ops) {
