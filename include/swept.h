@@ -298,7 +298,10 @@ swp_status swp_fit_width(int32_t eq, int64_t n_points, int32_t target, int32_t* 
  * (swp_fit_width; 0, the default rule, where the fitted width is not valid
  * for the problem) and problems[0..count) are advanced once by n_steps[i]
  * (swept, one persistent launch per group, block size `threads` as for
- * swp_batch_advance), timed with CUDA events on the batch's stream.  The
+ * swp_batch_advance), timed with CUDA events on the batch's stream (the
+ * span includes the host building and uploading the task tables, as a
+ * plain advance would).  A problem listed twice is rejected by the advance
+ * (SWP_EINVAL) after the states are saved, and put back.  The
  * fastest candidate's per-problem widths are written to widths_out[count],
  * its index to *best (may be NULL), and each candidate's milliseconds to
  * ms_out[n_candidates] (may be NULL).  The per-bucket autotuner
