@@ -317,3 +317,25 @@ def test_batch_tune_width_restores_states_and_returns_fitted_widths():
         O.classic(oprob(spec), ref, 1 + st)
         assert np.array_equal(p.read(), ref), (eq, bc, N, st, dtype)
         p.close()
+
+
+def test_batch_tune_width_errors_leave_states_unchanged():
+    """A problem listed twice fails in the trial advance (SWP_EINVAL) after
+    the states were saved, and they are put back; a candidate width <= 0
+    fails before anything runs."""
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    specs = [spec_for("ks", "periodic", 2053), spec_for("heat", "periodic", 1501)]
+    probs = [S.Problem(sp, state_for(sp, seed=3 + i), stream=stream) for i, sp in enumerate(specs)]
+    with S.Batch(stream) as b:
+        b.advance(probs, [3, 3])
+        b.synchronize()
+        before = [p.read() for p in probs]
+        with pytest.raises(S.SweptError, match="EINVAL"):
+            b.tune_width([probs[0], probs[1], probs[0]], [50, 50, 50], (256, 512))
+        with pytest.raises(S.SweptError, match="EINVAL"):
+            b.tune_width(probs, [50, 50], (256, 0))
+        for p, x in zip(probs, before):
+            assert np.array_equal(p.read(), x)
+    for p in probs:
+        p.close()
