@@ -511,7 +511,7 @@ def _serve(reqs, inputs, budget):
     of every result."""
     import threading
     from paper_1705_03162_gb300 import swept as S
-    with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=10.0) as srv:
+    with S.Server(hbm_budget_bytes=budget, max_active=256, round_target_ms=20.0) as srv:
         ids = [None] * len(reqs)
         t_start = time.perf_counter()
 
